@@ -308,10 +308,18 @@ static void discrete_convex(const float *P, int K, float delta, float sigma, flo
     float dp = g * delta;
     float sp = g * sigma;
     memcpy(&out->depth_bits, &depth, 4);
-    /* 4. opacity threshold: o*I >= tau needs o/tau - 1 > 0 */
-    float ot = opacity / st->tau;
-    float x = ot - 1.0f;
-    if (!(x > 0.0f)) { out->reason = R_OPACITY; return; }
+    /* 4. opacity threshold: o*I >= tau needs o/tau - 1 > 0 (with tau = 0 every pair counts) */
+    float x = 0.0f;
+    int full = 0;
+    if (st->tau > 0.0f) {
+        float ot = opacity / st->tau;
+        x = ot - 1.0f;
+        if (!(x > 0.0f)) { out->reason = R_OPACITY; return; }
+        if (!isfinite(x)) full = 1;
+    } else {
+        if (!(opacity > 0.0f)) { out->reason = R_OPACITY; return; }
+        full = 1;
+    }
     /* 5. hull */
     int T = orc_hull2d(&out->uv[0][0], K, out->idx);
     if (T < 3) { out->reason = R_HULL; return; }
@@ -333,10 +341,13 @@ static void discrete_convex(const float *P, int K, float delta, float sigma, flo
     }
     /* 7. radius r with {o I >= tau} inside {max_t L_t <= r}: from phi >= d delta max_t L_t,
           r = ln(o/tau - 1) / (d sigma * d delta); padded, then the mitre offset of the hull. */
-    float lnx = orc_ln_spec(x);
-    float prod = sp * dp;
-    float r = lnx / prod;
-    int full = !isfinite(r);
+    float r = 0.0f;
+    if (!full) {
+        float lnx = orc_ln_spec(x);
+        float prod = sp * dp;
+        r = lnx / prod;
+        if (!isfinite(r)) full = 1;
+    }
     if (r < 0.0f) r = 0.0f;
     float rp = r * 1.0009765625f;
     rp = rp + 0.00390625f;
