@@ -1,0 +1,159 @@
+/*
+ * convex_splat.h -- C ABI of the GB300 (sm_103a) differentiable tile rasterizer for 3D smooth
+ * convexes (3D Convex Splatting, arXiv 2411.14974).
+ *
+ * The library renders a set of N smooth convexes, each the convex hull of K free 3D points
+ * (Sec. 3.2, "point-based 3D convex shape representation"), into one or more pinhole views, and
+ * computes the gradient of a scalar loss with respect to the points, delta, sigma, opacity and
+ * spherical-harmonic colour (Sec. 3.3, "We optimize the position of each point set in 3D, delta
+ * and sigma parameters, the opacity o, and the spherical harmonic color coefficients").
+ *
+ * Per view and convex: the K points are projected (Eq. 4, with the perspective divide), their
+ * 2D convex hull is found by Graham scan with exact orientation predicates (Sec. 3.2), the hull
+ * edges become lines L_t(q) = n_t . q + c_t with outward unit normals (2D form of Eq. 1), and
+ * delta and sigma are multiplied by d^dist_power, d the camera distance (Sec. 3.2 last paragraph,
+ * supplementary Eq. S1/S2).  Convexes are binned into 16x16 pixel tiles and sorted by increasing
+ * camera distance to their centre (Sec. 3.2), and every pixel q composites front to back
+ * (Eq. 5) with
+ *     phi(q)   = log sum_t exp(d delta L_t(q))           (Eq. 2 / S1)
+ *     I(q)     = Sigmoid(-d sigma phi(q))                (Eq. 3 / S2)
+ *     alpha    = min(alpha_max, o I(q)),  skipped if alpha < tau
+ *     C(q)    += T alpha c,  T *= (1 - alpha),  stop once T < t_min (after accumulating)
+ *     C(q)    += T bg  at the end
+ * where c = max(0, sum_lm sh_lm Y_lm(dir) + 0.5) is the view-dependent colour (Sec. 3.2, real
+ * SH up to degree 3, dir from the camera centre to the convex centre).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" are CUDA device memory on the context's device, owned by the
+ *     caller; the library never frees them and only reads inputs / writes outputs.
+ *   - Pointers named "host" are ordinary (preferably pinned) host memory owned by the caller.
+ *   - Layouts are dense, C order, float32 unless stated:
+ *       points  [N][K][3], delta/sigma/opacity [N], sh [N][(D+1)^2][3]   (D = sh_degree)
+ *       image   [V][3][H][W] (channel planes), t_final [V][H][W]
+ *   - Every call returns a cs_status and never aborts, throws or traps.  On failure
+ *     cs_last_error() (thread-local) describes the cause.  Asynchronous device errors are
+ *     reported by the next call that synchronises.
+ *   - The stream argument is a cudaStream_t (0 = legacy default stream).  Work is enqueued on it;
+ *     cs_forward synchronises the stream once (to size the tile-pair buffers).
+ */
+#ifndef CONVEX_SPLAT_H
+#define CONVEX_SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CS_OK = 0,
+    CS_ERR_ARG = 1,      /* invalid argument (null pointer, size, unsupported setting) */
+    CS_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    CS_ERR_NOMEM = 3,    /* device or host allocation failed */
+    CS_ERR_BUDGET = 4,   /* a serving request does not fit the memory budget */
+    CS_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
+    CS_ERR_DEVICE = 6,   /* a kernel reported an error through the device status word */
+    CS_ERR_STATE = 7     /* object used in the wrong state (e.g. released, unknown id) */
+} cs_status;
+
+/* Pinhole camera (Eq. 4).  World -> camera rotation R (row major) and translation t, OpenCV axes
+   (x right, y down, z forward).  Pixel (i, j) is sampled at (i + 0.5, j + 0.5); a point maps to
+   (fx x/z + cx, fy y/z + cy).  Convexes with any point at z < z_near are not drawn. */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float z_near;
+} cs_camera;
+
+/* Compositing constants.  The paper's Eq. 5 has none; these follow the 3DGS tile rasterizer the
+   paper builds on (Sec. 3.2).  cs_default_settings(): tau = 1/255, alpha_max = 0.99,
+   t_min = 1e-4, bg = 0, dist_mode = 0, dist_power = 1. */
+typedef struct {
+    float tau;          /* pairs with alpha < tau add nothing; 0 <= tau < 1 */
+    float alpha_max;    /* alpha = min(alpha_max, o I); 0 < alpha_max <= 1 */
+    float t_min;        /* compositing stops once T < t_min (after accumulating); 0 <= t_min < 1 */
+    float bg[3];        /* background colour added with the final transmittance */
+    int32_t dist_mode;  /* d = |R c + t| (0) or the camera z of c (1); c = mean of the K points */
+    float dist_power;   /* delta, sigma scaled by d^p, p in {0, 0.5, 1, 2} (supp. Sec. C ablation) */
+} cs_settings;
+
+/* A scene: device pointers to N convexes with K points each (3 <= K <= 8) and SH degree D (0..3).
+   delta, sigma > 0 and opacity in (0, 1] are activated values (the paper activates with exp and
+   sigmoid, Sec. 3.3).  Convexes with non-finite or non-positive delta/sigma are not drawn. */
+typedef struct {
+    const float *points;
+    const float *delta;
+    const float *sigma;
+    const float *opacity;
+    const float *sh;
+    int64_t n;
+    int32_t k;
+    int32_t sh_degree;
+} cs_scene;
+
+typedef struct cs_context cs_context;      /* per-device library state: stream-ordered memory pool */
+typedef struct cs_fwd_state cs_fwd_state;  /* what a forward keeps for its backward */
+
+/* Fill *s with the defaults listed above. */
+void cs_default_settings(cs_settings *s);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *cs_last_error(void);
+
+/* Create a context on CUDA device `device`.  The context owns a stream-ordered memory pool for
+   the transient buffers of every call made with it.  Returns CS_ERR_CUDA if the device cannot be
+   used (no GPU, wrong architecture). */
+cs_status cs_context_create(int32_t device, cs_context **out);
+void cs_context_destroy(cs_context *ctx);
+
+/* Forward render (Sec. 3.2, Eq. 4, 5, S1, S2) of `scene` into n_views views of equal size.
+   cams:    host array [n_views]; all views must have the same width and height.
+   image:   device [n_views][3][H][W], written.
+   t_final: device [n_views][H][W] final transmittance, written; may be NULL.
+   state_out: if not NULL, receives a new state holding what cs_backward needs (the sorted
+            tile-pair lists, per-convex screen records, per-pixel T_final and last contributor);
+            release it with cs_state_release.  The scene buffers must stay alive and unchanged
+            until the backward has run.
+   Errors: CS_ERR_ARG for bad sizes/settings, CS_ERR_NOMEM, CS_ERR_CUDA. */
+cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs_camera *cams, int32_t n_views,
+                     const cs_settings *settings, float *image, float *t_final, cs_fwd_state **state_out,
+                     void *stream);
+
+/* Backward of cs_forward: given dL/dimage (device, same layout as image) accumulate (+=) the
+   gradient into the caller's device buffers dpoints [N][K][3], ddelta [N], dsigma [N],
+   dopacity [N], dsh [N][(D+1)^2][3] (any may be NULL to skip it; none may alias).  Reverse-order
+   compositing recomputes the transmittance from T_final (no per-pair storage); per-convex
+   gradients are reduced within each warp before global atomics.  Kinks take the one-sided value
+   0: clamped alpha, colour clamped at 0, skipped pairs. */
+cs_status cs_backward(cs_context *ctx, const cs_fwd_state *state, const float *dL_dimage, float *dpoints,
+                      float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream);
+
+/* Release a state (its device buffers return to the context's pool on the state's stream). */
+void cs_state_release(cs_fwd_state *state);
+
+/* Internal arrays of a forward state, copied to host memory for inspection and parity checks.
+   which: see cs_array.  host_dst may be NULL to query the size.  Synchronous. */
+typedef enum {
+    CS_ARR_RECORDS = 0,      /* float [R][32]: per (view, convex) screen record, see DESIGN */
+    CS_ARR_DEPTH_KEYS = 1,   /* uint32 [R]: binary32 bits of the camera distance; 0xffffffff if not drawn */
+    CS_ARR_RECTS = 2,        /* uint32 [R][2]: tile range (tx0 | tx1 << 16, ty0 | ty1 << 16) */
+    CS_ARR_COUNTS = 3,       /* uint32 [R]: number of tiles in the range (0 if not drawn) */
+    CS_ARR_PAIR_KEYS = 4,    /* uint32 [P]: global tile index of each sorted pair */
+    CS_ARR_PAIR_VALUES = 5,  /* uint32 [P]: record index (view * N + convex) of each sorted pair */
+    CS_ARR_TILE_RANGES = 6,  /* uint32 [tiles][2]: [start, end) of each tile in the pair list */
+    CS_ARR_N_LAST = 7,       /* uint32 [V][H][W]: 1 + pair index of the last contributor, 0 if none */
+    CS_ARR_HULLS = 8         /* uint32 [R]: hull size T in bits 0-3, vertex i in bits 4+3i.. */
+} cs_array;
+cs_status cs_state_copy(const cs_fwd_state *state, int32_t which, void *host_dst, size_t capacity,
+                        size_t *bytes_out);
+
+/* Numbers of records R (= n_views * N), sorted pairs P and tiles of a forward state. */
+cs_status cs_state_sizes(const cs_fwd_state *state, int64_t *records, int64_t *pairs, int64_t *tiles);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONVEX_SPLAT_H */

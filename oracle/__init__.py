@@ -73,7 +73,7 @@ def lib():
         _lib.orc_render_pixels.restype = ctypes.c_int
         _lib.orc_render_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, u64, P, P, P, P, P]
         _lib.orc_backward_pixels.restype = ctypes.c_int
-        _lib.orc_backward_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, P, P, P, P, P, P]
+        _lib.orc_backward_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, P, u64, P, P, P, P, P]
         _lib.orc_alpha_support.restype = ctypes.c_int
         _lib.orc_alpha_support.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P]
         _lib.orc_sh_basis.restype = None
@@ -190,8 +190,11 @@ def render_image(scene, cam, st=None, perturb_seed: int = 0) -> dict:
                 n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W))
 
 
-def backward_pixels(scene, cam, st, pix, dL_dC) -> dict:
-    """Analytic binary64 gradient of sum_i dL_dC[i] . C(pix[i]) w.r.t. points, delta, sigma, opacity, SH."""
+def backward_pixels(scene, cam, st, pix, dL_dC, perturb_seed: int = 0) -> dict:
+    """Analytic binary64 gradient of sum_i dL_dC[i] . C(pix[i]) w.r.t. points, delta, sigma, opacity, SH.
+
+    perturb_seed != 0 moves the projected points by 4 binary32 ulps in the per-pixel part (a
+    conditioning probe, as in render_pixels)."""
     st = st or settings()
     a, n, k, deg = _scene_arrays(scene)
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
@@ -203,18 +206,18 @@ def backward_pixels(scene, cam, st, pix, dL_dC) -> dict:
     c = camera(cam)
     rc = lib().orc_backward_pixels(_p(a["points"]), n, k, _p(a["delta"]), _p(a["sigma"]), _p(a["opacity"]),
                                    _p(a["sh"]), deg, ctypes.byref(c), ctypes.byref(st), _p(pix), pix.shape[0],
-                                   _p(g), _p(out["points"]), _p(out["delta"]), _p(out["sigma"]),
+                                   _p(g), int(perturb_seed), _p(out["points"]), _p(out["delta"]), _p(out["sigma"]),
                                    _p(out["opacity"]), _p(out["sh"]))
     if rc:
         raise ValueError(f"orc_backward_pixels failed ({rc})")
     return out
 
 
-def backward_image(scene, cam, st, dL_dimage) -> dict:
+def backward_image(scene, cam, st, dL_dimage, perturb_seed: int = 0) -> dict:
     """Gradient for a full-image cotangent dL_dimage [3][H][W]."""
     H, W = cam.height, cam.width
     g = np.asarray(dL_dimage, np.float64).reshape(3, H, W).transpose(1, 2, 0).reshape(-1, 3)
-    return backward_pixels(scene, cam, st, all_pixels(W, H), g)
+    return backward_pixels(scene, cam, st, all_pixels(W, H), g, perturb_seed)
 
 
 def alpha_support(scene, cam, st=None) -> np.ndarray:
@@ -256,3 +259,35 @@ def tile_lists(disc: dict, cam) -> dict:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def sorted_pairs(disc: dict, cam, tile_base: int = 0, rec_base: int = 0):
+    """Expected sorted (tile, record) pairs of one view: visible convexes in (depth bits, id) order
+    each list the tiles of their range in row-major order, then a stable sort by tile index.
+    Returns (keys = tile_base + tile index, values = rec_base + convex id)."""
+    vis = np.nonzero(disc["visible"])[0]
+    order = vis[np.lexsort((vis, disc["depth_bits"][vis]))]
+    r = disc["rect"][order].astype(np.int64)
+    nx = r[:, 2] - r[:, 0] + 1
+    ny = r[:, 3] - r[:, 1] + 1
+    cnt = nx * ny
+    rep = np.repeat(np.arange(len(order)), cnt)
+    within = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    tx = r[rep, 0] + within % nx[rep]
+    ty = r[rep, 1] + within // nx[rep]
+    keys = ty * ((cam.width + 15) // 16) + tx
+    vals = order[rep]
+    perm = np.argsort(keys, kind="stable")
+    return (keys[perm] + tile_base).astype(np.int64), (vals[perm] + rec_base).astype(np.int64)
+
+
+def pack_hull(disc: dict) -> np.ndarray:
+    """Hull of every convex in the packed form T | idx_i << (4 + 3 i); 0 when not drawn."""
+    out = np.zeros(len(disc["visible"]), np.uint32)
+    for i in np.nonzero(disc["visible"])[0]:
+        T = int(disc["hull_t"][i])
+        w = T
+        for j in range(T):
+            w |= int(disc["hull_idx"][i][j]) << (4 + 3 * j)
+        out[i] = w
+    return out

@@ -877,9 +877,10 @@ static void convex_chain(const float *P, int K, float delta, float sigma, const 
 int orc_backward_pixels(const float *points, int64_t n, int32_t k, const float *delta, const float *sigma,
                         const float *opacity, const float *sh, int32_t sh_deg, const orc_camera *cam,
                         const orc_settings *st, const int32_t *pix, int64_t npix, const double *dL_dC,
-                        double *dpoints, double *ddelta, double *dsigma, double *dopacity, double *dsh) {
+                        uint64_t perturb_seed, double *dpoints, double *ddelta, double *dsigma, double *dopacity,
+                        double *dsh) {
     orc_prepared pr;
-    int rc = prepare(&pr, points, n, k, delta, sigma, opacity, sh, sh_deg, cam, st, 0);
+    int rc = prepare(&pr, points, n, k, delta, sigma, opacity, sh, sh_deg, cam, st, perturb_seed);
     if (rc) { release(&pr); return rc; }
     orc_cgrad *cg = (orc_cgrad *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_cgrad));
     orc_hit *hits = (orc_hit *)malloc(sizeof(orc_hit) * (size_t)(pr.n_order > 0 ? pr.n_order : 1));

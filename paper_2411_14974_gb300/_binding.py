@@ -1,0 +1,72 @@
+"""ctypes declarations of the C ABI in include/convex_splat.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB
+
+
+class CsCamera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("z_near", ctypes.c_float)]
+
+
+class CsSettings(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float)]
+
+
+class CsScene(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("delta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+
+
+# every entry point declared in include/convex_splat.h, with (restype, argtypes)
+_P = ctypes.c_void_p
+_PROTOTYPES = {
+    "cs_default_settings": (None, [ctypes.POINTER(CsSettings)]),
+    "cs_last_error": (ctypes.c_char_p, []),
+    "cs_context_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P)]),
+    "cs_context_destroy": (None, [_P]),
+    "cs_forward": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera), ctypes.c_int32,
+                                  ctypes.POINTER(CsSettings), _P, _P, ctypes.POINTER(_P), _P]),
+    "cs_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cs_state_release": (None, [_P]),
+    "cs_state_copy": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_state_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library; fails loudly if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        handle = ctypes.CDLL(LIB)
+        for name, (res, args) in _PROTOTYPES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_symbols():
+    return list(_PROTOTYPES)
+
+
+class CsError(RuntimeError):
+    pass
+
+
+def check(code: int, what: str):
+    if code != 0:
+        msg = lib().cs_last_error().decode(errors="replace")
+        raise CsError(f"{what} failed (status {code}): {msg}")

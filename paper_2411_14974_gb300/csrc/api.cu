@@ -1,0 +1,482 @@
+// C-ABI entry points of the convex tile rasterizer: context, forward, backward, state access.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "cs_api_internal.h"
+#include "cs_common.cuh"
+
+using namespace cs;
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+cs_status cs::fail(cs_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cs_status cs::fail_cuda(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky launch error so the next call starts clean
+    return fail(CS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char *cs_last_error(void) { return g_err; }
+
+extern "C" void cs_default_settings(cs_settings *s) {
+    if (!s) return;
+    s->tau = 1.0f / 255.0f;
+    s->alpha_max = 0.99f;
+    s->t_min = 1e-4f;
+    s->bg[0] = s->bg[1] = s->bg[2] = 0.f;
+    s->dist_mode = 0;
+    s->dist_power = 1.0f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// context and stream-ordered allocations
+// ---------------------------------------------------------------------------------------------
+extern "C" cs_status cs_context_create(int32_t device, cs_context **out) {
+    if (!out) return fail(CS_ERR_ARG, "cs_context_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= count) return fail(CS_ERR_ARG, "device %d out of range (%d devices)", device, count);
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(CS_ERR_CUDA, "device %d is sm_%d%d; this library is built for sm_103a only", device, prop.major,
+                    prop.minor);
+    int prev = 0;
+    cudaGetDevice(&prev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaSetDevice");
+    cs_context *c = new (std::nothrow) cs_context();
+    if (!c) return fail(CS_ERR_NOMEM, "out of host memory");
+    c->device = device;
+    c->sm_count = prop.multiProcessorCount;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&c->pool, &props);
+    if (e != cudaSuccess) {
+        delete c;
+        cudaSetDevice(prev);
+        return fail_cuda(e, "cudaMemPoolCreate");
+    }
+    uint64_t keep = UINT64_MAX;  // keep freed memory in the pool: later calls reuse it without the driver
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    e = cudaMallocHost(&c->host_total, sizeof(unsigned long long) * 2);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(c->pool);
+        delete c;
+        cudaSetDevice(prev);
+        return fail_cuda(e, "cudaMallocHost");
+    }
+    cudaSetDevice(prev);
+    *out = c;
+    return CS_OK;
+}
+
+extern "C" void cs_context_destroy(cs_context *ctx) {
+    if (!ctx) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->host_total) cudaFreeHost(ctx->host_total);
+    cudaMemPoolTrimTo(ctx->pool, 0);
+    cudaMemPoolDestroy(ctx->pool);
+    cudaSetDevice(prev);
+    delete ctx;
+}
+
+cudaError_t cs::pool_alloc(cs_context *ctx, void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    return cudaMallocFromPoolAsync(p, (bytes + 255) & ~(size_t)255, ctx->pool, s);
+}
+
+void cs::pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// validation helpers
+// ---------------------------------------------------------------------------------------------
+cs_status cs::check_settings(const cs_settings *st) {
+    if (!st) return fail(CS_ERR_ARG, "settings is NULL");
+    if (!(st->tau >= 0.f && st->tau < 1.f)) return fail(CS_ERR_ARG, "tau must be in [0, 1)");
+    if (!(st->alpha_max > 0.f && st->alpha_max <= 1.f)) return fail(CS_ERR_ARG, "alpha_max must be in (0, 1]");
+    if (!(st->t_min >= 0.f && st->t_min < 1.f)) return fail(CS_ERR_ARG, "t_min must be in [0, 1)");
+    if (st->dist_mode != 0 && st->dist_mode != 1) return fail(CS_ERR_ARG, "dist_mode must be 0 or 1");
+    const float p = st->dist_power;
+    if (!(p == 0.f || p == 0.5f || p == 1.f || p == 2.f)) return fail(CS_ERR_ARG, "dist_power must be 0, 0.5, 1 or 2");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(st->bg[i])) return fail(CS_ERR_ARG, "bg must be finite");
+    return CS_OK;
+}
+
+cs_status cs::check_camera(const cs_camera *c) {
+    if (c->width <= 0 || c->height <= 0 || c->width > 32768 || c->height > 32768)
+        return fail(CS_ERR_ARG, "camera size %dx%d out of range (1..32768)", c->width, c->height);
+    const float v[] = {c->fx, c->fy, c->cx, c->cy, c->z_near};
+    for (float x : v)
+        if (!isfinite(x)) return fail(CS_ERR_ARG, "camera intrinsics must be finite");
+    for (int i = 0; i < 9; ++i)
+        if (!isfinite(c->R[i])) return fail(CS_ERR_ARG, "camera R must be finite");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(c->t[i])) return fail(CS_ERR_ARG, "camera t must be finite");
+    if (!(c->z_near > 0.f)) return fail(CS_ERR_ARG, "z_near must be > 0");
+    return CS_OK;
+}
+
+cs_status cs::check_scene(const cs_scene *s) {
+    if (!s) return fail(CS_ERR_ARG, "scene is NULL");
+    if (s->n < 0 || s->n > (int64_t)1 << 31) return fail(CS_ERR_ARG, "scene size %lld out of range", (long long)s->n);
+    if (s->k < 3 || s->k > KMAX) return fail(CS_ERR_ARG, "k = %d: 3 <= k <= 8 points per convex", s->k);
+    if (s->sh_degree < 0 || s->sh_degree > 3) return fail(CS_ERR_ARG, "sh_degree must be 0..3");
+    if (s->n > 0 && (!s->points || !s->delta || !s->sigma || !s->opacity || !s->sh))
+        return fail(CS_ERR_ARG, "scene has a NULL buffer");
+    return CS_OK;
+}
+
+void cs::fill_view(ViewDesc &vd, const cs_camera &c) {
+    memset(&vd, 0, sizeof vd);
+    memcpy(vd.R, c.R, sizeof vd.R);
+    memcpy(vd.t, c.t, sizeof vd.t);
+    vd.fx = c.fx; vd.fy = c.fy; vd.cx = c.cx; vd.cy = c.cy; vd.z_near = c.z_near;
+    for (int a = 0; a < 3; ++a)
+        vd.campos[a] = (float)(-((double)c.R[a] * c.t[0] + (double)c.R[3 + a] * c.t[1] + (double)c.R[6 + a] * c.t[2]));
+    vd.width = c.width;
+    vd.height = c.height;
+    vd.tiles_x = (c.width + TILE - 1) / TILE;
+    vd.tiles_y = (c.height + TILE - 1) / TILE;
+}
+
+Settings cs::to_settings(const cs_settings &s) {
+    Settings o;
+    o.tau = s.tau; o.alpha_max = s.alpha_max; o.t_min = s.t_min;
+    o.bg[0] = s.bg[0]; o.bg[1] = s.bg[1]; o.bg[2] = s.bg[2];
+    o.dist_mode = s.dist_mode; o.dist_power = s.dist_power;
+    return o;
+}
+
+// ---------------------------------------------------------------------------------------------
+// forward pipeline over a batch of views
+// ---------------------------------------------------------------------------------------------
+#define CS_TRY(expr, what)                               \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) {                         \
+            st_code = fail_cuda(_e, what);               \
+            goto cleanup;                                \
+        }                                                \
+    } while (0)
+
+void cs::state_free(cs_fwd_state *s) {
+    if (!s) return;
+    cudaStream_t st = s->stream;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->ctx->device);
+    pool_free(s->views_dev, st);
+    pool_free(s->records, st);
+    pool_free(s->depth_keys, st);
+    pool_free(s->rects, st);
+    pool_free(s->counts, st);
+    pool_free(s->pair_keys, st);
+    pool_free(s->pair_vals, st);
+    pool_free(s->ranges, st);
+    pool_free(s->n_last, st);
+    pool_free(s->t_final_own, st);
+    cudaSetDevice(prev);
+    delete s;
+}
+
+static int bits_for(uint64_t n) {
+    int b = 0;
+    while (b < 32 && ((uint64_t)1 << b) < n) ++b;
+    return b;
+}
+
+cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream) {
+    cs_status st_code = CS_OK;
+    const int V = (int)s->views.size();
+    int64_t R = 0, max_n = 0;
+    uint32_t tiles = 0;
+    for (int v = 0; v < V; ++v) {
+        ViewDesc &vd = s->views[v];
+        vd.rec_base = R;
+        vd.tile_base = tiles;
+        R += vd.n;
+        max_n = vd.n > max_n ? vd.n : max_n;
+        tiles += (uint32_t)(vd.tiles_x * vd.tiles_y);
+    }
+    s->n_records = R;
+    s->n_tiles = tiles;
+    s->stream = stream;
+    size_t pix_total = 0;
+    for (int v = 0; v < V; ++v) pix_total += (size_t)s->views[v].width * s->views[v].height;
+
+    uint32_t *sort_keys_a = nullptr, *sort_keys_b = nullptr, *sort_vals_a = nullptr, *sort_vals_b = nullptr;
+    uint32_t *offsets = nullptr, *radix_tmp = nullptr, *pk_b = nullptr, *pv_b = nullptr;
+    unsigned long long *scan_tmp = nullptr, *total = nullptr;
+    uint64_t P = 0;
+    bool in_b = false;
+    const int tile_bits = bits_for(tiles);
+
+    CS_TRY(pool_alloc(ctx, (void **)&s->views_dev, sizeof(ViewDesc) * V, stream), "alloc views");
+    CS_TRY(pool_alloc(ctx, (void **)&s->records, (size_t)R * REC_WORDS * 4, stream), "alloc records");
+    CS_TRY(pool_alloc(ctx, (void **)&s->depth_keys, (size_t)R * 4, stream), "alloc depth keys");
+    CS_TRY(pool_alloc(ctx, (void **)&s->rects, (size_t)R * 8, stream), "alloc rects");
+    CS_TRY(pool_alloc(ctx, (void **)&s->counts, (size_t)R * 4, stream), "alloc counts");
+    CS_TRY(pool_alloc(ctx, (void **)&s->ranges, (size_t)tiles * 8, stream), "alloc ranges");
+    CS_TRY(pool_alloc(ctx, (void **)&s->n_last, pix_total * 4, stream), "alloc n_last");
+    {
+        bool need_t = false;
+        for (int v = 0; v < V; ++v) need_t |= s->views[v].t_final == nullptr;
+        if (need_t) {
+            CS_TRY(pool_alloc(ctx, (void **)&s->t_final_own, pix_total * 4, stream), "alloc t_final");
+        }
+        size_t off = 0;
+        for (int v = 0; v < V; ++v) {
+            ViewDesc &vd = s->views[v];
+            const size_t np = (size_t)vd.width * vd.height;
+            vd.n_last = s->n_last + off;
+            if (!vd.t_final) vd.t_final = s->t_final_own + off;
+            off += np;
+        }
+    }
+    CS_TRY(cudaMemcpyAsync(s->views_dev, s->views.data(), sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, stream),
+           "copy views");
+    {
+        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts};
+        CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
+    }
+    // depth order of the records
+    {
+        const size_t scan_words = scan_tmp_words(R > 256 * 8 ? R : 256 * 8) + scan_tmp_words(256 * ((R + 4095) / 4096 + 1));
+        CS_TRY(pool_alloc(ctx, (void **)&sort_keys_a, (size_t)R * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&sort_keys_b, (size_t)R * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&sort_vals_a, (size_t)R * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&sort_vals_b, (size_t)R * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&offsets, (size_t)R * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words(R) * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_words * 8, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&total, 16, stream), "alloc");
+        if (R > 0) {
+            CS_TRY(cudaMemcpyAsync(sort_keys_a, s->depth_keys, (size_t)R * 4, cudaMemcpyDeviceToDevice, stream),
+                   "copy keys");
+        }
+        CS_TRY(launch_iota(sort_vals_a, R, stream), "iota");
+        CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, 32, radix_tmp, scan_tmp, &in_b,
+                                stream),
+               "depth sort");
+        uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;
+        CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, total, scan_tmp, stream), "scan");
+        CS_TRY(cudaMemcpyAsync(ctx->host_total, total, 8, cudaMemcpyDeviceToHost, stream), "read pair count");
+        CS_TRY(cudaStreamSynchronize(stream), "synchronize");
+        P = ctx->host_total[0];
+        if (P >= 0xffffffffull) {
+            st_code = fail(CS_ERR_ARG, "%llu tile pairs exceed the 32-bit pair index", (unsigned long long)P);
+            goto cleanup;
+        }
+        s->n_pairs = (int64_t)P;
+        CS_TRY(pool_alloc(ctx, (void **)&s->pair_keys, P * 4, stream), "alloc pairs");
+        CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");
+        CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
+        CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
+        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, R, s->pair_keys, s->pair_vals,
+                                 stream),
+               "emit pairs");
+    }
+    // stable sort of the pairs by tile
+    {
+        pool_free(radix_tmp, stream);
+        pool_free(scan_tmp, stream);
+        radix_tmp = nullptr;
+        scan_tmp = nullptr;
+        const int64_t nbk = ((int64_t)P + 4095) / 4096;
+        CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words((int64_t)P) * 4, stream), "alloc");
+        CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_tmp_words(256 * (nbk + 1)) * 8, stream), "alloc");
+        CS_TRY(radix_sort_pairs(s->pair_keys, s->pair_vals, pk_b, pv_b, (int64_t)P, tile_bits, radix_tmp, scan_tmp,
+                                &in_b, stream),
+               "tile sort");
+        if (in_b) {
+            uint32_t *t = s->pair_keys; s->pair_keys = pk_b; pk_b = t;
+            t = s->pair_vals; s->pair_vals = pv_b; pv_b = t;
+        }
+        CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->ranges, tiles, stream), "tile ranges");
+    }
+    {
+        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, tiles};
+        CS_TRY(launch_blend_forward(a, stream), "blend");
+    }
+cleanup:
+    pool_free(sort_keys_a, stream);
+    pool_free(sort_keys_b, stream);
+    pool_free(sort_vals_a, stream);
+    pool_free(sort_vals_b, stream);
+    pool_free(offsets, stream);
+    pool_free(radix_tmp, stream);
+    pool_free(scan_tmp, stream);
+    pool_free(total, stream);
+    pool_free(pk_b, stream);
+    pool_free(pv_b, stream);
+    return st_code;
+}
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        cudaSetDevice(d);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+extern "C" cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs_camera *cams, int32_t n_views,
+                                const cs_settings *settings, float *image, float *t_final, cs_fwd_state **state_out,
+                                void *stream_ptr) {
+    if (state_out) *state_out = nullptr;
+    if (!ctx) return fail(CS_ERR_ARG, "context is NULL");
+    cs_status st;
+    if ((st = check_scene(scene)) != CS_OK) return st;
+    if ((st = check_settings(settings)) != CS_OK) return st;
+    if (!cams || n_views <= 0 || n_views > 1024) return fail(CS_ERR_ARG, "need 1..1024 cameras");
+    if (!image) return fail(CS_ERR_ARG, "image is NULL");
+    for (int v = 0; v < n_views; ++v) {
+        if ((st = check_camera(&cams[v])) != CS_OK) return st;
+        if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+            return fail(CS_ERR_ARG, "cs_forward: all views must have the same size");
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    cs_fwd_state *s = new (std::nothrow) cs_fwd_state();
+    if (!s) return fail(CS_ERR_NOMEM, "out of host memory");
+    s->ctx = ctx;
+    s->scene = *scene;
+    s->k = scene->k;
+    s->st = to_settings(*settings);
+    s->settings = *settings;
+    s->views.resize(n_views);
+    const size_t hw = (size_t)cams[0].width * cams[0].height;
+    for (int v = 0; v < n_views; ++v) {
+        ViewDesc &vd = s->views[v];
+        fill_view(vd, cams[v]);
+        vd.points = scene->points; vd.delta = scene->delta; vd.sigma = scene->sigma;
+        vd.opacity = scene->opacity; vd.sh = scene->sh;
+        vd.n = scene->n; vd.k = scene->k; vd.sh_degree = scene->sh_degree;
+        vd.image = image + (size_t)v * 3 * hw;
+        vd.t_final = t_final ? t_final + (size_t)v * hw : nullptr;
+    }
+    st = run_forward(ctx, s, stream);
+    if (st != CS_OK || !state_out) {
+        state_free(s);
+        return st;
+    }
+    *state_out = s;
+    return CS_OK;
+}
+
+extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
+                                 float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream_ptr) {
+    if (!ctx || !s) return fail(CS_ERR_ARG, "context or state is NULL");
+    if (s->ctx != ctx) return fail(CS_ERR_STATE, "state belongs to another context");
+    if (!dL_dimage) return fail(CS_ERR_ARG, "dL_dimage is NULL");
+    if (s->settings.alpha_max > 0.999f)
+        return fail(CS_ERR_ARG, "the backward needs alpha_max <= 0.999 (T is recovered by dividing by 1 - alpha)");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    const int V = (int)s->views.size();
+    cs_status st_code = CS_OK;
+    float4 *grads = nullptr;
+    if (s->n_records == 0) return CS_OK;
+    {
+        cudaError_t e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);
+        if (e != cudaSuccess) return fail_cuda(e, "alloc gradient records");
+        e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
+        if (e == cudaSuccess) {
+            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, s->n_tiles};
+            const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
+            e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
+        }
+        if (e == cudaSuccess) {
+            PreprocessGrads g{dpoints, ddelta, dsigma, dopacity, dsh};
+            e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->st, s->records, s->counts, grads, g,
+                                           V > 1, stream);
+        }
+        if (e != cudaSuccess) st_code = fail_cuda(e, "backward");
+    }
+    pool_free(grads, stream);
+    return st_code;
+}
+
+extern "C" void cs_state_release(cs_fwd_state *s) { state_free(s); }
+
+extern "C" cs_status cs_state_sizes(const cs_fwd_state *s, int64_t *records, int64_t *pairs, int64_t *tiles) {
+    if (!s) return fail(CS_ERR_ARG, "state is NULL");
+    if (records) *records = s->n_records;
+    if (pairs) *pairs = s->n_pairs;
+    if (tiles) *tiles = s->n_tiles;
+    return CS_OK;
+}
+
+extern "C" cs_status cs_state_copy(const cs_fwd_state *s, int32_t which, void *host_dst, size_t capacity,
+                                   size_t *bytes_out) {
+    if (!s) return fail(CS_ERR_ARG, "state is NULL");
+    const void *src = nullptr;
+    size_t bytes = 0;
+    size_t pix = 0;
+    for (const ViewDesc &vd : s->views) pix += (size_t)vd.width * vd.height;
+    switch (which) {
+        case CS_ARR_RECORDS: src = s->records; bytes = (size_t)s->n_records * REC_WORDS * 4; break;
+        case CS_ARR_DEPTH_KEYS: src = s->depth_keys; bytes = (size_t)s->n_records * 4; break;
+        case CS_ARR_RECTS: src = s->rects; bytes = (size_t)s->n_records * 8; break;
+        case CS_ARR_COUNTS: src = s->counts; bytes = (size_t)s->n_records * 4; break;
+        case CS_ARR_PAIR_KEYS: src = s->pair_keys; bytes = (size_t)s->n_pairs * 4; break;
+        case CS_ARR_PAIR_VALUES: src = s->pair_vals; bytes = (size_t)s->n_pairs * 4; break;
+        case CS_ARR_TILE_RANGES: src = s->ranges; bytes = (size_t)s->n_tiles * 8; break;
+        case CS_ARR_N_LAST: src = s->n_last; bytes = pix * 4; break;
+        case CS_ARR_HULLS: break;
+        default: return fail(CS_ERR_ARG, "unknown array %d", which);
+    }
+    if (which == CS_ARR_HULLS) bytes = (size_t)s->n_records * 4;
+    if (bytes_out) *bytes_out = bytes;
+    if (!host_dst) return CS_OK;
+    if (capacity < bytes) return fail(CS_ERR_ARG, "capacity %zu < %zu bytes", capacity, bytes);
+    DeviceGuard dg(s->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "synchronize");
+    if (which == CS_ARR_HULLS) {
+        // word 7 of every record; records that are not drawn report 0
+        std::vector<uint32_t> rec((size_t)s->n_records * REC_WORDS), cnt((size_t)s->n_records);
+        if (s->n_records) {
+            e = cudaMemcpy(rec.data(), s->records, rec.size() * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), s->counts, cnt.size() * 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return fail_cuda(e, "copy");
+        }
+        uint32_t *d = (uint32_t *)host_dst;
+        for (int64_t r = 0; r < s->n_records; ++r) d[r] = cnt[r] ? rec[(size_t)r * REC_WORDS + R_HULL] : 0u;
+        return CS_OK;
+    }
+    if (bytes) {
+        e = cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(e, "copy");
+    }
+    return CS_OK;
+}

@@ -1,0 +1,50 @@
+// Host-side objects behind the C-ABI handles.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "cs_common.cuh"
+
+struct cs_context {
+    int device = 0;
+    int sm_count = 0;
+    cudaMemPool_t pool = nullptr;             // stream-ordered pool for every transient buffer
+    unsigned long long *host_total = nullptr; // pinned readback slot for the pair count
+};
+
+struct cs_fwd_state {
+    cs_context *ctx = nullptr;
+    cudaStream_t stream = nullptr;  // stream of the forward; buffers are freed on it
+    cs_scene scene{};
+    int k = 0;
+    cs_settings settings{};
+    cs::Settings st{};
+    std::vector<cs::ViewDesc> views;  // host copy (with device pointers filled in)
+    cs::ViewDesc *views_dev = nullptr;
+    int64_t n_records = 0, n_pairs = 0;
+    uint32_t n_tiles = 0;
+    float4 *records = nullptr;
+    uint32_t *depth_keys = nullptr;
+    uint2 *rects = nullptr;
+    uint32_t *counts = nullptr;
+    uint32_t *pair_keys = nullptr, *pair_vals = nullptr;
+    uint2 *ranges = nullptr;
+    uint32_t *n_last = nullptr;
+    float *t_final_own = nullptr;
+};
+
+namespace cs {
+cs_status fail(cs_status st, const char *fmt, ...);
+cs_status fail_cuda(cudaError_t e, const char *what);
+cudaError_t pool_alloc(cs_context *ctx, void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+cs_status check_settings(const cs_settings *st);
+cs_status check_camera(const cs_camera *c);
+cs_status check_scene(const cs_scene *s);
+void fill_view(ViewDesc &vd, const cs_camera &c);
+Settings to_settings(const cs_settings &s);
+cs_status run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream);
+void state_free(cs_fwd_state *s);
+}  // namespace cs

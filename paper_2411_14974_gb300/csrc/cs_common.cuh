@@ -1,0 +1,111 @@
+// Internal definitions shared by the CUDA sources of the convex tile rasterizer (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/convex_splat.h"
+
+namespace cs {
+
+constexpr int KMAX = 8;    // most points per convex
+constexpr int TILE = 16;   // tile edge in pixels
+constexpr int REC_WORDS = 32;   // 128-byte screen record per (view, convex)
+constexpr int GRAD_WORDS = 32;  // 128-byte gradient record per (view, convex)
+
+// Screen record layout (32-bit words), written by the preprocess, read by both blends:
+//   0, 1   anchor a = first hull vertex (pixels); lines below are expressed relative to it
+//   2      sigma' = d^p sigma
+//   3      opacity o
+//   4..6   colour c (after the clamp at 0)
+//   7      hull: T in bits 0-3, index of hull vertex i in bits 4+3i..6+3i
+//   8+3t   A_t = kappa n_t.x          kappa = log2(e) d^p delta, so that
+//   9+3t   B_t = kappa n_t.y          kappa L_t(q) = A_t (q.x - a.x) + B_t (q.y - a.y) + C_t
+//   10+3t  C_t = kappa n_t . (a - v_t)
+constexpr int R_AX = 0, R_AY = 1, R_SIG = 2, R_OPA = 3, R_RGB = 4, R_HULL = 7, R_LINES = 8;
+
+// Gradient record layout: d(loss)/d(screen record quantities)
+//   3t+0..2  dA_t, dB_t, dC_t     24 dsigma'    25 dopacity    26..28 dcolour
+constexpr int G_SIG = 24, G_OPA = 25, G_RGB = 26;
+
+struct ViewDesc {
+    // camera
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, z_near;
+    float campos[3];  // camera centre in world coordinates (-R^T t), for the SH direction
+    int32_t width, height, tiles_x, tiles_y;
+    uint32_t tile_base;  // first global tile index of this view
+    int64_t rec_base;    // first record index of this view
+    // scene (device)
+    const float *points, *delta, *sigma, *opacity, *sh;
+    int64_t n;
+    int32_t k, sh_degree;
+    // outputs (device)
+    float *image;     // [3][H][W]
+    float *t_final;   // [H][W]
+    uint32_t *n_last; // [H][W]
+};
+
+struct Settings {
+    float tau, alpha_max, t_min;
+    float bg[3];
+    int32_t dist_mode;
+    float dist_power;
+};
+
+__host__ __device__ inline uint32_t hull_pack_count(uint32_t packed) { return packed & 15u; }
+__host__ __device__ inline int hull_pack_index(uint32_t packed, int i) { return (int)((packed >> (4 + 3 * i)) & 7u); }
+
+// ---- launch wrappers implemented in the .cu files --------------------------------------------
+struct PreprocessOut {
+    float4 *records;       // [R][8]
+    uint32_t *depth_keys;  // [R]
+    uint2 *rects;          // [R]
+    uint32_t *counts;      // [R]
+};
+cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n,
+                              int k, const Settings &st, const PreprocessOut &out, cudaStream_t s);
+
+struct PreprocessGrads {
+    float *dpoints, *ddelta, *dsigma, *dopacity, *dsh;
+};
+cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k,
+                                       const Settings &st, const float4 *records, const uint32_t *counts,
+                                       const float4 *grad_records, const PreprocessGrads &g, bool atomic,
+                                       cudaStream_t s);
+
+// device-wide exclusive scan of n uint32 values (optionally gathered through idx); writes the
+// 64-bit total to *total_dev.  tmp must hold scan_tmp_words(n) uint64 words.
+size_t scan_tmp_words(int64_t n);
+cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out, int64_t n,
+                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s);
+
+// stable LSD radix sort of (key, value) pairs on the low `bits` key bits.  Buffers a/b alternate;
+// returns in *result_in_b whether the sorted data ended in the b buffers.
+size_t radix_tmp_words(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
+                             int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
+                             cudaStream_t s);
+
+cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s);
+cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
+                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
+cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, uint2 *ranges, int64_t n_tiles,
+                               cudaStream_t s);
+
+struct BlendArgs {
+    const ViewDesc *views;
+    int n_views;
+    const uint2 *ranges;
+    const uint32_t *pair_vals;
+    const float4 *records;
+    Settings st;
+    uint32_t n_tiles;
+};
+cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s);
+cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,
+                                  float4 *grad_records, cudaStream_t s);
+
+}  // namespace cs

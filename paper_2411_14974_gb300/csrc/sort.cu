@@ -1,0 +1,308 @@
+// Binning and sorting for the convex tile rasterizer (Sec. 3.2: convexes are binned into tiles
+// and drawn in order of increasing camera distance to their centres).
+//
+//   1. records sorted by depth key (binary32 bits of the distance, stable, so equal depths keep
+//      increasing record index = convex index within a view);
+//   2. exclusive scan of the per-record tile counts in that order;
+//   3. each record emits (global tile index, record index) pairs, tiles in row-major order;
+//   4. stable radix sort of the pairs by tile index: every tile's list ends up in (depth, index)
+//      order, the same order a single sort on (tile, depth, index) would give;
+//   5. [start, end) range of every tile in the sorted pair list.
+//
+// The radix sort is a three-kernel LSD sort (digit histogram per tile of 4096 keys, scan of the
+// digit-major histogram, stable scatter).  Ranks inside a block come from warp-level key matching
+// (__match_any_sync) over warp-striped runs of keys, so the scatter is stable.
+#include "cs_common.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SPINE_THREADS = 1024;
+
+constexpr int RADIX_THREADS = 256;
+constexpr int RADIX_WARPS = RADIX_THREADS / 32;
+constexpr int RADIX_ITEMS = 16;
+constexpr int RADIX_TILE = RADIX_THREADS * RADIX_ITEMS;  // 4096 keys per block
+constexpr int RADIX_MAX_BITS = 8;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---- scan -----------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long *sh,
+                                                                   unsigned long long &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (w == 0) {
+        unsigned long long s = lane < nw ? sh[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long warp_prefix = w > 0 ? sh[w - 1] : 0ull;
+    total = sh[nw - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t *gather, int64_t i, int64_t n) {
+    if (i >= n) return 0u;
+    return gather ? in[gather[i]] : in[i];
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                              const uint32_t *__restrict__ gather, int64_t n,
+                                                              unsigned long long *__restrict__ partial) {
+    __shared__ unsigned long long sh[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) s += scan_load(in, gather, base + j * SCAN_THREADS + threadIdx.x, n);
+    unsigned long long total;
+    block_exclusive_scan(s, sh, total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(unsigned long long *__restrict__ partial, int64_t nb,
+                                                              unsigned long long *__restrict__ total_out) {
+    __shared__ unsigned long long sh[32];
+    unsigned long long carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += SPINE_THREADS) {
+        const int64_t i = b0 + threadIdx.x;
+        const unsigned long long v = i < nb ? partial[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_exclusive_scan(v, sh, tot);
+        if (i < nb) partial[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ gather, int64_t n,
+                                                            const unsigned long long *__restrict__ partial,
+                                                            uint32_t *__restrict__ out) {
+    __shared__ unsigned long long sh[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;  // blocked
+    uint32_t v[SCAN_ITEMS];
+    unsigned long long s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = scan_load(in, gather, base + j, n);
+        s += v[j];
+    }
+    unsigned long long tot;
+    unsigned long long run = block_exclusive_scan(s, sh, tot) + partial[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < n) out[base + j] = (uint32_t)run;
+        run += v[j];
+    }
+}
+
+// ---- radix sort -----------------------------------------------------------------------------
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t *__restrict__ keys, int64_t n,
+                                                                 int shift, int nbits, uint32_t *__restrict__ hist,
+                                                                 int64_t nblocks) {
+    __shared__ uint32_t cnt[RADIX_WARPS][1 << RADIX_MAX_BITS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nbins = 1u << nbits, mask = nbins - 1;
+    for (int i = threadIdx.x; i < RADIX_WARPS * (1 << RADIX_MAX_BITS); i += RADIX_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t seg = (int64_t)blockIdx.x * RADIX_TILE + (int64_t)w * (RADIX_ITEMS * 32);
+#pragma unroll 4
+    for (int j = 0; j < RADIX_ITEMS; ++j) {
+        const int64_t idx = seg + j * 32 + lane;
+        const uint32_t d = idx < n ? (keys[idx] >> shift) & mask : 0xffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d != 0xffffu && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < nbins; d += RADIX_THREADS) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int q = 0; q < RADIX_WARPS; ++q) s += cnt[q][d];
+        hist[(int64_t)d * nblocks + blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t *__restrict__ keys_in,
+                                                                 const uint32_t *__restrict__ vals_in, int64_t n,
+                                                                 int shift, int nbits,
+                                                                 const uint32_t *__restrict__ offsets,
+                                                                 int64_t nblocks, uint32_t *__restrict__ keys_out,
+                                                                 uint32_t *__restrict__ vals_out) {
+    __shared__ uint32_t cnt[RADIX_WARPS][1 << RADIX_MAX_BITS];
+    __shared__ uint32_t gbase[1 << RADIX_MAX_BITS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t nbins = 1u << nbits, mask = nbins - 1;
+    for (int i = threadIdx.x; i < RADIX_WARPS * (1 << RADIX_MAX_BITS); i += RADIX_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t seg = (int64_t)blockIdx.x * RADIX_TILE + (int64_t)w * (RADIX_ITEMS * 32);
+    const uint32_t lt = lanemask_lt();
+    uint32_t key[RADIX_ITEMS], val[RADIX_ITEMS], dr[RADIX_ITEMS];
+#pragma unroll
+    for (int j = 0; j < RADIX_ITEMS; ++j) {
+        const int64_t idx = seg + j * 32 + lane;
+        const bool valid = idx < n;
+        key[j] = valid ? keys_in[idx] : 0u;
+        val[j] = valid ? vals_in[idx] : 0u;
+        const uint32_t d = valid ? (key[j] >> shift) & mask : 0xffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t base = 0;
+        if (valid) base = cnt[w][d];
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[w][d] = base + __popc(peers);
+        __syncwarp();
+        dr[j] = valid ? ((base + __popc(peers & lt)) << 9) | d : 0xffffffffu;
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < nbins; d += RADIX_THREADS) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int q = 0; q < RADIX_WARPS; ++q) {
+            const uint32_t c = cnt[q][d];
+            cnt[q][d] = run;
+            run += c;
+        }
+        gbase[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RADIX_ITEMS; ++j) {
+        if (dr[j] == 0xffffffffu) continue;
+        const uint32_t d = dr[j] & 511u, r = dr[j] >> 9;
+        const uint32_t dst = gbase[d] + cnt[w][d] + r;
+        keys_out[dst] = key[j];
+        vals_out[dst] = val[j];
+    }
+}
+
+// ---- pairs ----------------------------------------------------------------------------------
+__global__ void k_iota(uint32_t *v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
+                       const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
+                       const uint2 *__restrict__ rects, int64_t n_records, uint32_t *__restrict__ keys,
+                       uint32_t *__restrict__ vals) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_records) return;
+    const uint32_t r = sorted[j];
+    if (counts[r] == 0) return;
+    const uint2 rc = rects[r];
+    const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
+    int v = 0;
+    while (v + 1 < n_views && (int64_t)r >= views[v + 1].rec_base) ++v;
+    const uint32_t tile_base = views[v].tile_base, tiles_x = (uint32_t)views[v].tiles_x;
+    uint32_t o = offsets[j];
+    for (uint32_t ty = ty0; ty <= ty1; ++ty)
+        for (uint32_t tx = tx0; tx <= tx1; ++tx) {
+            keys[o] = tile_base + ty * tiles_x + tx;
+            vals[o] = r;
+            ++o;
+        }
+}
+
+__global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, uint2 *__restrict__ ranges) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+}
+
+}  // namespace
+
+size_t scan_tmp_words(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1; }
+
+cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather, uint32_t *out, int64_t n,
+                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
+        return cudaSuccess;
+    }
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp);
+    k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(tmp, nb, total_dev);
+    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out);
+    return cudaGetLastError();
+}
+
+size_t radix_tmp_words(int64_t n) {
+    const int64_t nb = (n + RADIX_TILE - 1) / RADIX_TILE;
+    return (size_t)(nb * (1 << RADIX_MAX_BITS) * 2);
+}
+
+cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
+                             int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
+                             cudaStream_t s) {
+    *result_in_b = false;
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    const int64_t nb = (n + RADIX_TILE - 1) / RADIX_TILE;
+    const int passes = (bits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
+    uint32_t *hist = tmp;
+    uint32_t *offs = tmp + nb * (1 << RADIX_MAX_BITS);
+    uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
+    int shift = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int w = (bits - shift + (passes - p) - 1) / (passes - p);  // spread the bits evenly
+        const int64_t nh = (int64_t)(1 << w) * nb;
+        k_radix_upsweep<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, n, shift, w, hist, nb);
+        cudaError_t e = launch_exclusive_scan(hist, nullptr, offs, nh, nullptr, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, vin, n, shift, w, offs, nb, kout, vout);
+        shift += w;
+        uint32_t *t;
+        t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+        *result_in_b = !*result_in_b;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
+                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
+    if (n_records <= 0) return cudaSuccess;
+    k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
+                                                               rects, n_records, pair_keys, pair_vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, uint2 *ranges, int64_t n_tiles,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+    if (e != cudaSuccess || n_pairs <= 0) return e;
+    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

@@ -1,0 +1,211 @@
+"""GPU forward parity with the oracle, through the C ABI.
+
+Bit-exact: visibility, hull vertex indices, tile ranges, depth keys and the sorted tile-pair lists
+(Sec. 3.2).  Within 1e-4 per channel: the images (Eq. 5), outside the conditioning mask (pixels
+whose binary64 value moves by more than 2.5e-5 when the projected points move by 4 binary32
+ulps, or where a cut-off decision is within its band).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_14974_gb300 import synthetic as syn
+from tests import _cases as C
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _pack_rect(r):
+    r = r.astype(np.uint64)
+    return np.stack([r[:, 0] | (r[:, 2] << 16), r[:, 1] | (r[:, 3] << 16)], 1).astype(np.uint32)
+
+
+def check_discrete(state, sc, cam, rec_base=0, tile_base=0, **kw):
+    disc = oracle.discrete(sc, cam, oracle.settings(**kw))
+    n = sc.n
+    dk = state.array("depth_keys")[rec_base:rec_base + n]
+    cnt = state.array("counts")[rec_base:rec_base + n]
+    rects = state.array("rects").reshape(-1, 2)[rec_base:rec_base + n]
+    hulls = state.array("hulls")[rec_base:rec_base + n]
+    vis = disc["visible"].astype(bool)
+    assert ((cnt > 0) == vis).all(), "visibility differs"
+    assert (dk[vis] == disc["depth_bits"][vis]).all(), "depth keys differ"
+    assert (dk[~vis] == 0xFFFFFFFF).all()
+    assert (hulls == oracle.pack_hull(disc)).all(), "hull vertex indices differ"
+    assert (rects[vis] == _pack_rect(disc["rect"][vis])).all(), "tile ranges differ"
+    r = disc["rect"][vis].astype(np.int64)
+    assert (cnt[vis] == (r[:, 2] - r[:, 0] + 1) * (r[:, 3] - r[:, 1] + 1)).all()
+    return disc
+
+
+def check_pairs(state, discs, cams):
+    keys, vals = [], []
+    tb, rb = 0, 0
+    for disc, cam in zip(discs, cams):
+        k, v = oracle.sorted_pairs(disc, cam, tb, rb)
+        keys.append(k)
+        vals.append(v)
+        tb += ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+        rb += len(disc["visible"])
+    keys = np.concatenate(keys)
+    vals = np.concatenate(vals)
+    gk = state.array("pair_keys").astype(np.int64)
+    gv = state.array("pair_values").astype(np.int64)
+    assert len(gk) == len(keys), f"{len(gk)} pairs, expected {len(keys)}"
+    assert (gk == keys).all(), "pair tile keys differ"
+    assert (gv == vals).all(), "pair order differs"
+    rng = state.array("tile_ranges").reshape(-1, 2).astype(np.int64)
+    cnt = np.bincount(keys, minlength=tb)
+    nz = cnt > 0
+    assert (rng[nz, 1] - rng[nz, 0] == cnt[nz]).all()
+    assert (rng[~nz] == 0).all()
+    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    assert (rng[nz, 0] == starts[nz]).all()
+
+
+def check_image(img, ref, ill, max_ill=0.02):
+    d = np.abs(img - ref["image"]).max(0)
+    frac = float(ill.mean())
+    assert frac <= max_ill, f"{frac:.4f} of the pixels are ill-conditioned"
+    worst = float(d[~ill].max()) if (~ill).any() else 0.0
+    assert worst <= P.IMAGE_TOL, f"max |gpu - oracle| = {worst:.3e} on well-conditioned pixels"
+    return worst, frac
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blob1k_128_discrete_and_order(seed):
+    sc, cams = syn.workload("blob1k_128", seed=seed)
+    img, tf, state, _ = P.gpu_render(sc, cams)
+    disc = check_discrete(state, sc, cams[0])
+    check_pairs(state, [disc], cams)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blob1k_128_image(seed):
+    sc, cams = syn.workload("blob1k_128", seed=seed)
+    ref, ill = P.oracle_reference(sc, cams[0])
+    img, tf, state, _ = P.gpu_render(sc, cams)
+    check_image(img[0], ref, ill)
+    assert np.abs(tf[0] - ref["t_final"])[~ill].max() <= P.IMAGE_TOL
+
+
+def test_well_conditioned_needs_no_mask():
+    sc, cams = syn.workload("blob1k_128", seed=3)
+    rng = np.random.default_rng(3)
+    sc.sigma = np.exp(rng.uniform(np.log(0.01), np.log(0.3), sc.n)).astype(np.float32)
+    sc.delta = np.exp(rng.uniform(np.log(0.5), np.log(5.0), sc.n)).astype(np.float32)
+    ref, ill = P.oracle_reference(sc, cams[0])
+    img, _, _, _ = P.gpu_render(sc, cams, keep_state=False)
+    d = np.abs(img[0] - ref["image"]).max(0)
+    flag = (ref["flags"] & 3) != 0  # only cut-off decisions within their band are excluded
+    assert flag.mean() < 0.01
+    assert d[~flag].max() <= P.IMAGE_TOL
+
+
+@pytest.mark.parametrize("w,h", [(100, 75), (17, 33), (1, 1), (129, 16)])
+def test_ragged_sizes(w, h):
+    sc, _ = syn.workload("blob1k_128", seed=4)
+    cam = syn.blob_camera(w, h)
+    ref, ill = P.oracle_reference(sc, cam)
+    img, _, state, _ = P.gpu_render(sc, [cam])
+    disc = check_discrete(state, sc, cam)
+    check_pairs(state, [disc], [cam])
+    check_image(img[0], ref, ill, max_ill=0.05 if w * h > 64 else 1.0)
+
+
+@pytest.mark.parametrize("k,deg", [(3, 1), (4, 2), (5, 3), (7, 0), (8, 3)])
+def test_points_per_convex_and_sh_degree(k, deg):
+    sc = syn.blob_scene(5 + k, n=600, k=k, radius=0.08, sh_degree=deg)
+    cam = syn.blob_camera(96, 80)
+    ref, ill = P.oracle_reference(sc, cam)
+    img, _, state, _ = P.gpu_render(sc, [cam])
+    disc = check_discrete(state, sc, cam)
+    check_pairs(state, [disc], [cam])
+    check_image(img[0], ref, ill)
+
+
+@pytest.mark.parametrize("kw", [dict(dist_power=0.0), dict(dist_power=0.5), dict(dist_power=2.0),
+                                dict(dist_mode=1), dict(tau=0.02, t_min=1e-3, bg=(0.2, 0.5, 1.0)),
+                                dict(alpha_max=0.5)])
+def test_settings_variants(kw):
+    sc, cams = syn.workload("blob1k_128", seed=6)
+    if kw.get("dist_power") == 2.0:
+        sc.delta /= 4.0
+        sc.sigma /= 4.0
+    ref, ill = P.oracle_reference(sc, cams[0], **kw)
+    img, _, state, _ = P.gpu_render(sc, cams, **kw)
+    disc = check_discrete(state, sc, cams[0], **kw)
+    check_pairs(state, [disc], cams)
+    check_image(img[0], ref, ill, max_ill=0.05)
+
+
+def test_tau_zero_full_screen_ranges():
+    sc = syn.blob_scene(7, n=60, radius=0.1)
+    cam = syn.blob_camera(64, 48)
+    kw = dict(tau=0.0, t_min=0.0)
+    ref, ill = P.oracle_reference(sc, cam, **kw)
+    img, _, state, _ = P.gpu_render(sc, [cam], **kw)
+    disc = check_discrete(state, sc, cam, **kw)
+    assert disc["full"][disc["visible"] == 1].all()
+    assert state.sizes()["pairs"] == int(disc["visible"].sum()) * 4 * 3
+    check_pairs(state, [disc], [cam])
+    check_image(img[0], ref, ill, max_ill=0.05)
+
+
+def test_empty_and_fully_culled_scenes():
+    cam = syn.blob_camera(40, 24)
+    empty = syn.Scene(np.zeros((0, 6, 3), np.float32), np.zeros(0, np.float32), np.zeros(0, np.float32),
+                      np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    img, tf, state, _ = P.gpu_render(empty, [cam], bg=(0.25, 0.5, 0.75))
+    assert np.allclose(img[0], np.array([0.25, 0.5, 0.75], np.float32)[:, None, None].astype(np.float64))
+    assert (tf == 1).all() and state.sizes()["pairs"] == 0
+    sc = syn.blob_scene(8, n=50)
+    sc.points[..., 2] -= 10.0  # everything behind the camera
+    img, tf, state, _ = P.gpu_render(sc, [cam])
+    assert (img == 0).all() and (tf == 1).all() and state.sizes()["pairs"] == 0
+    assert (state.array("counts") == 0).all()
+
+
+def test_nonfinite_and_invalid_parameters_are_culled():
+    sc = syn.blob_scene(9, n=200)
+    sc.points[0, 0, 0] = np.nan
+    sc.delta[1] = -1.0
+    sc.sigma[2] = np.inf
+    sc.opacity[3] = 0.0
+    cam = syn.blob_camera()
+    ref, ill = P.oracle_reference(sc, cam)
+    img, _, state, _ = P.gpu_render(sc, [cam])
+    disc = check_discrete(state, sc, cam)
+    assert not disc["visible"][:4].any()
+    check_image(img[0], ref, ill)
+
+
+def test_multi_view_equals_single_views():
+    """Views are binned and sorted together (view index in the tile key); each view's image is the
+    same, bit for bit, as rendering it alone."""
+    sc = syn.surface_scene(11, n=20_000, sh_degree=3)
+    cams = syn.sphere_cameras(3, 160, 120, 4.0, seed=12)
+    img, _, state, _ = P.gpu_render(sc, cams)
+    discs = [check_discrete(state, sc, c, rec_base=i * sc.n) for i, c in enumerate(cams)]
+    check_pairs(state, discs, cams)
+    for v, cam in enumerate(cams):
+        one, _, _, _ = P.gpu_render(sc, [cam], keep_state=False)
+        assert (one[0] == img[v]).all()
+
+
+def test_surface_scene_image_sh3():
+    sc = syn.surface_scene(13, n=30_000, sh_degree=3)
+    cam = syn.sphere_cameras(1, 200, 150, 4.0, seed=14)[0]
+    ref, ill = P.oracle_reference(sc, cam)
+    img, _, state, _ = P.gpu_render(sc, [cam])
+    check_discrete(state, sc, cam)
+    check_image(img[0], ref, ill, max_ill=0.05)
+
+
+def test_square_worked_example_on_gpu():
+    sc = C.square_scene()
+    cam = C.axis_camera()
+    img, _, _, _ = P.gpu_render(sc, [cam], tau=0.0, alpha_max=1.0, t_min=0.0)
+    I, _ = C.square_indicator_closed_form(128, 128, 63.5, 8.0, 2.0, 0.5)
+    assert np.abs(img[0, 0] - 0.5 * I).max() < 1e-5
