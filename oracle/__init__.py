@@ -50,7 +50,8 @@ class OrcCamera(ctypes.Structure):
 
 class OrcSettings(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float)]
+                ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float),
+                ("q_binary32", ctypes.c_int32), ("perturb_ulps", ctypes.c_float), ("line_rel", ctypes.c_float)]
 
 
 _lib = None
@@ -71,7 +72,7 @@ def lib():
         _lib.orc_discrete.restype = ctypes.c_int
         _lib.orc_discrete.argtypes = [P, i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_render_pixels.restype = ctypes.c_int
-        _lib.orc_render_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, u64, P, P, P, P, P]
+        _lib.orc_render_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, u64, P, P, P, P, P, P]
         _lib.orc_backward_pixels.restype = ctypes.c_int
         _lib.orc_backward_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, P, u64, P, P, P, P, P]
         _lib.orc_alpha_support.restype = ctypes.c_int
@@ -101,12 +102,22 @@ def camera(cam) -> OrcCamera:
 
 
 def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), dist_mode=0,
-             dist_power=1.0) -> OrcSettings:
+             dist_power=1.0, q_binary32=False, perturb_ulps=4.0, line_rel=0.0) -> OrcSettings:
+    """Method settings plus oracle-only knobs (no counterpart in the method).
+
+    q_binary32: build the hull lines from the binary32 projected points the hull was decided on
+    (the discrete specification) rather than from a binary64 re-projection; the continuous maths
+    stays binary64.
+    Error model for the conditioning bound ``sens``, the decision bands and the probes:
+      line_rel > 0: every line value may be off by line_rel (|q - a|_1 + |a - v_t|_1 + 32 + |L_t|)
+                    pixels (binary32 evaluation relative to the anchor vertex a);
+      otherwise:    every hull vertex may move by perturb_ulps binary32 ulps."""
     s = OrcSettings()
     s.tau, s.alpha_max, s.t_min = float(tau), float(alpha_max), float(t_min)
     for i in range(3):
         s.bg[i] = float(bg[i])
     s.dist_mode, s.dist_power = int(dist_mode), float(dist_power)
+    s.q_binary32, s.perturb_ulps, s.line_rel = int(bool(q_binary32)), float(perturb_ulps), float(line_rel)
     return s
 
 
@@ -170,24 +181,28 @@ def render_pixels(scene, cam, st=None, pix=None, perturb_seed: int = 0) -> dict:
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
     m = pix.shape[0]
     out = dict(rgb=np.zeros((m, 3)), t_final=np.zeros(m), last_id=np.zeros(m, np.int64),
-               n_contrib=np.zeros(m, np.int32), flags=np.zeros(m, np.uint32))
+               n_contrib=np.zeros(m, np.int32), flags=np.zeros(m, np.uint32), sens=np.zeros(m))
     c = camera(cam)
     rc = lib().orc_render_pixels(_p(a["points"]), n, k, _p(a["delta"]), _p(a["sigma"]), _p(a["opacity"]),
                                  _p(a["sh"]), deg, ctypes.byref(c), ctypes.byref(st), _p(pix), m,
                                  int(perturb_seed), _p(out["rgb"]), _p(out["t_final"]), _p(out["last_id"]),
-                                 _p(out["n_contrib"]), _p(out["flags"]))
+                                 _p(out["n_contrib"]), _p(out["flags"]), _p(out["sens"]))
     if rc:
         raise ValueError(f"orc_render_pixels failed ({rc})")
     return out
 
 
 def render_image(scene, cam, st=None, perturb_seed: int = 0) -> dict:
-    """Full image: rgb [3][H][W], t_final [H][W], last_id, n_contrib, flags [H][W]."""
+    """Full image: rgb [3][H][W], t_final [H][W], last_id, n_contrib, flags, sens [H][W].
+
+    sens is a first-order bound on how much any channel can change when every hull vertex moves
+    by perturb_ulps binary32 ulps; flags mark cut-off decisions within their bands."""
     r = render_pixels(scene, cam, st, None, perturb_seed)
     H, W = cam.height, cam.width
     return dict(image=np.ascontiguousarray(r["rgb"].reshape(H, W, 3).transpose(2, 0, 1)),
                 t_final=r["t_final"].reshape(H, W), last_id=r["last_id"].reshape(H, W),
-                n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W))
+                n_contrib=r["n_contrib"].reshape(H, W), flags=r["flags"].reshape(H, W),
+                sens=r["sens"].reshape(H, W))
 
 
 def backward_pixels(scene, cam, st, pix, dL_dC, perturb_seed: int = 0) -> dict:

@@ -64,13 +64,24 @@ typedef struct {
     float bg[3];     /* background colour */
     int32_t dist_mode;  /* 0: d = |R c + t|, 1: d = camera z of c */
     float dist_power;   /* 0, 0.5, 1 or 2 */
+    /* oracle-only knobs (no counterpart in the method):
+       q_binary32 = 1 builds the hull lines from the binary32 projected points on which the hull
+       was decided (the discrete specification's q), instead of a binary64 re-projection;
+       perturb_ulps is the size of the conditioning probe (see render_pixels). */
+    int32_t q_binary32;
+    float perturb_ulps;
+    /* line_rel > 0 selects the line-evaluation error model for the sensitivity bound and the
+       probes: each L_t(q) may be off by line_rel (|q - a|_1 + |a - v_t|_1 + 32 + |L_t|) pixels,
+       a = first hull vertex (the size of binary32 line evaluation relative to an anchor vertex);
+       otherwise the vertex-motion model (every hull vertex moves by perturb_ulps ulps) is used. */
+    float line_rel;
 } orc_settings;
 
 /* flags reported per pixel by the continuous render */
 #define ORC_FLAG_ALPHA_NEAR_TAU 1u  /* some evaluated alpha within ORC_ALPHA_BAND of tau */
 #define ORC_FLAG_T_NEAR_TMIN 2u     /* the transmittance came within a band of t_min */
 #define ORC_FLAG_CLAMP_NEAR 4u      /* some o*I within ORC_ALPHA_BAND of alpha_max */
-#define ORC_ALPHA_BAND 1e-5
+#define ORC_ALPHA_BAND 1e-6
 #define ORC_T_BAND_REL 1e-3
 
 /* ------------------------------------------------------------------------------------------ */
@@ -473,6 +484,8 @@ typedef struct {
     int T;
     int idx[ORC_KMAX];
     double n[ORC_KMAX][2], c0[ORC_KMAX]; /* L_t(q) = n_t . q + c0_t, outward unit normal, pixels */
+    double v[ORC_KMAX][2], elen[ORC_KMAX]; /* start vertex and length of each hull edge */
+    double eps;                            /* perturb_ulps binary32 ulps of the largest coordinate */
     double dp, sp;                       /* d^p delta, d^p sigma */
     double o;
     double rgb[3], raw[3];
@@ -509,16 +522,21 @@ static void continuous_convex(const float *P, int K, float delta, float sigma, f
                               uint64_t perturb_seed, int64_t id, orc_convex *cv) {
     double q[ORC_KMAX][2];
     for (int k = 0; k < K; k++) {
-        double p[3] = {P[3 * k], P[3 * k + 1], P[3 * k + 2]}, xc[3];
-        xform_f64(cam, p, xc);
-        q[k][0] = (double)cam->fx * xc[0] / xc[2] + (double)cam->cx;
-        q[k][1] = (double)cam->fy * xc[1] / xc[2] + (double)cam->cy;
-        if (perturb_seed) { /* conditioning probe: move each coordinate by 4 binary32 ulps */
+        if (st->q_binary32) {
+            q[k][0] = dsc->uv[k][0];
+            q[k][1] = dsc->uv[k][1];
+        } else {
+            double p[3] = {P[3 * k], P[3 * k + 1], P[3 * k + 2]}, xc[3];
+            xform_f64(cam, p, xc);
+            q[k][0] = (double)cam->fx * xc[0] / xc[2] + (double)cam->cx;
+            q[k][1] = (double)cam->fy * xc[1] / xc[2] + (double)cam->cy;
+        }
+        if (perturb_seed) { /* conditioning probe: move each coordinate by perturb_ulps binary32 ulps */
             for (int a = 0; a < 2; a++) {
                 uint64_t h = splitmix64(perturb_seed ^ (uint64_t)(id * 64 + k * 2 + a) * 0x2545f4914f6cdd1dull);
                 float f = fabsf((float)q[k][a]);
                 double ulp = (double)nextafterf(f, INFINITY) - (double)f;
-                q[k][a] += ((h & 1) ? 4.0 : -4.0) * ulp;
+                q[k][a] += ((h & 1) ? 1.0 : -1.0) * (double)st->perturb_ulps * ulp;
             }
         }
     }
@@ -544,6 +562,15 @@ static void continuous_convex(const float *P, int K, float delta, float sigma, f
         cv->n[i][0] = ey / len;
         cv->n[i][1] = -ex / len;
         cv->c0[i] = -(cv->n[i][0] * v[0] + cv->n[i][1] * v[1]);
+        cv->v[i][0] = v[0];
+        cv->v[i][1] = v[1];
+        cv->elen[i] = len;
+    }
+    {
+        float big = 0.0f;
+        for (int i = 0; i < dsc->T; i++)
+            for (int a = 0; a < 2; a++) big = fmaxf(big, fabsf((float)cv->v[i][a]));
+        cv->eps = (double)st->perturb_ulps * ((double)nextafterf(big, INFINITY) - (double)big);
     }
     double cp[3], wv[3];
     camera_centre(cam, cp);
@@ -571,6 +598,7 @@ static void continuous_convex(const float *P, int K, float delta, float sigma, f
 typedef struct {
     int64_t n;
     int32_t k, sh_deg;
+    uint64_t probe; /* line-model probe seed (0 = none) */
     orc_disc *dsc;
     orc_convex *cv;
     int64_t *order; /* visible convexes by (depth bits, id) */
@@ -590,6 +618,7 @@ static int prepare(orc_prepared *pr, const float *points, int64_t n, int32_t k, 
                    const orc_camera *cam, const orc_settings *st, uint64_t perturb_seed) {
     if (k < 3 || k > ORC_KMAX || n < 0 || sh_deg < 0 || sh_deg > 3) return -1;
     pr->n = n; pr->k = k; pr->sh_deg = sh_deg;
+    pr->probe = st->line_rel > 0.0f ? perturb_seed : 0;
     pr->dsc = (orc_disc *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_disc));
     pr->cv = (orc_convex *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_convex));
     pr->order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -600,7 +629,7 @@ static int prepare(orc_prepared *pr, const float *points, int64_t n, int32_t k, 
         discrete_convex(points + 3 * k * i, k, delta[i], sigma[i], opacity[i], cam, st, &pr->dsc[i]);
         if (pr->dsc[i].visible)
             continuous_convex(points + 3 * k * i, k, delta[i], sigma[i], opacity[i], sh + 3 * nb * i, sh_deg,
-                              cam, st, &pr->dsc[i], perturb_seed, i, &pr->cv[i]);
+                              cam, st, &pr->dsc[i], st->line_rel > 0.0f ? 0 : perturb_seed, i, &pr->cv[i]);
     }
     int64_t m = 0;
     for (int64_t i = 0; i < n; i++)
@@ -617,12 +646,45 @@ static void release(orc_prepared *pr) {
     free(pr->order);
 }
 
+/* Error model of one line value at pixel (x, y), in pixels (see line_rel / perturb_ulps). */
+static double line_error(const orc_convex *cv, const orc_settings *st, double x, double y, int t, double Lt) {
+    if (st->line_rel > 0.0f) {
+        const double ax = cv->v[0][0], ay = cv->v[0][1];
+        return (double)st->line_rel *
+               (fabs(x - ax) + fabs(y - ay) + fabs(ax - cv->v[t][0]) + fabs(ay - cv->v[t][1]) + 32.0 + fabs(Lt));
+    }
+    /* moving the endpoints of edge t by eps moves L_t(q) by at most 2 eps (2 + |q - v_t| / |e_t|) */
+    const double r = hypot(x - cv->v[t][0], y - cv->v[t][1]);
+    return 2.0 * cv->eps * (2.0 + r / cv->elen[t]);
+}
+
+/* Bound on how far alpha of this pair can move under the error model: phi moves by
+   d delta sum_t w_t dL_t (w = softmax weights of d delta L_t) plus the error of the
+   transcendental evaluation, and alpha = o I by o I (1 - I) d sigma times the phi change. */
+static double alpha_sensitivity(const orc_convex *cv, const orc_settings *st, double x, double y, const double *L,
+                                double I) {
+    double Lmax = -INFINITY, S = 0.0, dL = 0.0;
+    for (int t = 0; t < cv->T; t++) Lmax = fmax(Lmax, L[t]);
+    for (int t = 0; t < cv->T; t++) {
+        double w = exp(cv->dp * (L[t] - Lmax));
+        dL += w * line_error(cv, st, x, y, t, L[t]);
+        S += w;
+    }
+    const double dphi = cv->dp * (dL / S) + 1e-6;
+    return cv->o * I * (1.0 - I) * cv->sp * dphi + 1e-7;
+}
+
 /* evaluate the smooth indicator of convex cv at pixel position (x, y); returns 0 when the pair
    is provably below tau - band (no exponentials needed), else fills phi, I and the L_t. */
-static int indicator(const orc_convex *cv, double x, double y, double L[ORC_KMAX], double *phi, double *I) {
+static int indicator(const orc_convex *cv, const orc_settings *st, uint64_t probe, int64_t id, double x, double y,
+                     double L[ORC_KMAX], double *phi, double *I) {
     double Lmax = -INFINITY;
     for (int t = 0; t < cv->T; t++) {
         L[t] = cv->n[t][0] * x + cv->n[t][1] * y + cv->c0[t];
+        if (probe && st->line_rel > 0.0f) { /* conditioning probe of the line-evaluation model */
+            uint64_t h = splitmix64(probe ^ (uint64_t)(id * 16 + t) * 0x9e3779b97f4a7c15ull);
+            L[t] += ((h & 1) ? 1.0 : -1.0) * line_error(cv, st, x, y, t, L[t]);
+        }
         if (L[t] > Lmax) Lmax = L[t];
     }
     if (Lmax > cv->r_pre) return 0;
@@ -644,8 +706,10 @@ typedef struct {
 /* Eq. 5, front to back over the depth order, for one pixel.  When hits != NULL the contributing
    pairs are recorded (for the backward pass). */
 static void composite(const orc_prepared *pr, const orc_settings *st, double x, double y, double rgb[3],
-                      double *Tout, int64_t *last, int32_t *ncontrib, uint32_t *flags, orc_hit *hits) {
-    double C[3] = {0, 0, 0}, T = 1.0;
+                      double *Tout, int64_t *last, int32_t *ncontrib, uint32_t *flags, double *sens,
+                      orc_hit *hits) {
+    double C[3] = {0, 0, 0}, T = 1.0, dT = 0.0, sum_Tda = 0.0;
+    double cmax = fmax(fmax(fabs((double)st->bg[0]), fabs((double)st->bg[1])), fabs((double)st->bg[2]));
     int64_t lst = -1;
     int32_t nc = 0;
     uint32_t fl = 0;
@@ -653,12 +717,19 @@ static void composite(const orc_prepared *pr, const orc_settings *st, double x, 
         int64_t id = pr->order[j];
         const orc_convex *cv = &pr->cv[id];
         double L[ORC_KMAX], phi, I;
-        if (!indicator(cv, x, y, L, &phi, &I)) continue;
+        if (!indicator(cv, st, pr->probe, id, x, y, L, &phi, &I)) continue;
         double oI = cv->o * I;
         double a = oI < (double)st->alpha_max ? oI : (double)st->alpha_max;
-        if (fabs(a - (double)st->tau) < ORC_ALPHA_BAND) fl |= ORC_FLAG_ALPHA_NEAR_TAU;
-        if (fabs(oI - (double)st->alpha_max) < ORC_ALPHA_BAND) fl |= ORC_FLAG_CLAMP_NEAR;
+        /* decision bands: a fixed 1e-6 plus twice the vertex-motion sensitivity of alpha */
+        double da = alpha_sensitivity(cv, st, x, y, L, I);
+        double band = ORC_ALPHA_BAND + 2.0 * da;
+        if (st->tau > 0.0f && fabs(a - (double)st->tau) < band) fl |= ORC_FLAG_ALPHA_NEAR_TAU;
+        if (fabs(oI - (double)st->alpha_max) < band) fl |= ORC_FLAG_CLAMP_NEAR;
         if (a < (double)st->tau) continue;
+        const double da_eff = a < (double)st->alpha_max ? da : 0.0;
+        dT += da_eff / (1.0 - a);
+        sum_Tda += T * da_eff;
+        for (int ch = 0; ch < 3; ch++) cmax = fmax(cmax, cv->rgb[ch]);
         if (hits) {
             orc_hit *h = &hits[nc];
             h->id = id; h->alpha = a; h->Tb = T; h->I = I; h->phi = phi; h->oI = oI;
@@ -668,10 +739,14 @@ static void composite(const orc_prepared *pr, const orc_settings *st, double x, 
         T *= (1.0 - a);
         lst = id;
         nc++;
-        if (fabs(T - (double)st->t_min) < ORC_T_BAND_REL * (double)st->t_min) fl |= ORC_FLAG_T_NEAR_TMIN;
+        if (fabs(T - (double)st->t_min) < ORC_T_BAND_REL * (double)st->t_min + 2.0 * T * dT)
+            fl |= ORC_FLAG_T_NEAR_TMIN;
         if (T < (double)st->t_min) break;
     }
     for (int ch = 0; ch < 3; ch++) rgb[ch] = C[ch] + T * (double)st->bg[ch];
+    /* first-order bound on the change of any channel when the vertices move by eps:
+       |dC/dalpha_n| = |T_n c_n - S_n / (1 - alpha_n)| <= 2 T_n cmax, since S_n <= T_{n+1} cmax */
+    if (sens) *sens = 2.0 * cmax * sum_Tda;
     *Tout = T;
     *last = lst;
     *ncontrib = nc;
@@ -681,17 +756,19 @@ static void composite(const orc_prepared *pr, const orc_settings *st, double x, 
 int orc_render_pixels(const float *points, int64_t n, int32_t k, const float *delta, const float *sigma,
                       const float *opacity, const float *sh, int32_t sh_deg, const orc_camera *cam,
                       const orc_settings *st, const int32_t *pix, int64_t npix, uint64_t perturb_seed,
-                      double *rgb, double *t_final, int64_t *last_id, int32_t *n_contrib, uint32_t *flags) {
+                      double *rgb, double *t_final, int64_t *last_id, int32_t *n_contrib, uint32_t *flags,
+                      double *sens) {
     orc_prepared pr;
     int rc = prepare(&pr, points, n, k, delta, sigma, opacity, sh, sh_deg, cam, st, perturb_seed);
     if (rc) { release(&pr); return rc; }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < npix; i++) {
-        double c[3], T;
+        double c[3], T, sv;
         int64_t lst;
         int32_t nc;
         uint32_t fl;
-        composite(&pr, st, pix[2 * i] + 0.5, pix[2 * i + 1] + 0.5, c, &T, &lst, &nc, &fl, NULL);
+        composite(&pr, st, pix[2 * i] + 0.5, pix[2 * i + 1] + 0.5, c, &T, &lst, &nc, &fl, &sv, NULL);
+        if (sens) sens[i] = sv;
         for (int ch = 0; ch < 3; ch++) rgb[3 * i + ch] = c[ch];
         if (t_final) t_final[i] = T;
         if (last_id) last_id[i] = lst;
@@ -717,7 +794,7 @@ int orc_alpha_support(const float *points, int64_t n, int32_t k, const float *de
             for (int y = 0; y < cam->height; y++)
                 for (int x = 0; x < cam->width; x++) {
                     double L[ORC_KMAX], phi, I;
-                    if (!indicator(&pr.cv[i], x + 0.5, y + 0.5, L, &phi, &I)) continue;
+                    if (!indicator(&pr.cv[i], st, 0, i, x + 0.5, y + 0.5, L, &phi, &I)) continue;
                     double a = pr.cv[i].o * I;
                     if (a > (double)st->alpha_max) a = st->alpha_max;
                     if (a < (double)st->tau) continue;
@@ -749,7 +826,7 @@ static void pixel_backward(const orc_prepared *pr, const orc_settings *st, doubl
     int64_t lst;
     int32_t nc;
     uint32_t fl;
-    composite(pr, st, x, y, c, &Tf, &lst, &nc, &fl, hits);
+    composite(pr, st, x, y, c, &Tf, &lst, &nc, &fl, NULL, hits);
     /* S accumulates, from the back, the colour seen behind the current pair: sum of later
        T_m alpha_m c_m plus T_final * bg. */
     double S[3];
@@ -792,14 +869,19 @@ static void pixel_backward(const orc_prepared *pr, const orc_settings *st, doubl
 
 /* chain the per-convex gradient back to points, delta, sigma, opacity and SH */
 static void convex_chain(const float *P, int K, float delta, float sigma, const float *sh, int sh_deg,
-                         const orc_camera *cam, const orc_settings *st, const orc_convex *cv, const orc_cgrad *g,
-                         double *dP, double *ddelta, double *dsigma, double *dopa, double *dsh) {
+                         const orc_camera *cam, const orc_settings *st, const orc_disc *dsc, const orc_convex *cv,
+                         const orc_cgrad *g, double *dP, double *ddelta, double *dsigma, double *dopa, double *dsh) {
     double xc[ORC_KMAX][3], q[ORC_KMAX][2], dq[ORC_KMAX][2];
     for (int k = 0; k < K; k++) {
         double p[3] = {P[3 * k], P[3 * k + 1], P[3 * k + 2]};
         xform_f64(cam, p, xc[k]);
-        q[k][0] = (double)cam->fx * xc[k][0] / xc[k][2] + (double)cam->cx;
-        q[k][1] = (double)cam->fy * xc[k][1] / xc[k][2] + (double)cam->cy;
+        if (st->q_binary32) {
+            q[k][0] = dsc->uv[k][0];
+            q[k][1] = dsc->uv[k][1];
+        } else {
+            q[k][0] = (double)cam->fx * xc[k][0] / xc[k][2] + (double)cam->cx;
+            q[k][1] = (double)cam->fy * xc[k][1] / xc[k][2] + (double)cam->cy;
+        }
         dq[k][0] = dq[k][1] = 0.0;
     }
     /* lines: n = (ey, -ex)/|e|, c0 = -n.v, e = w - v */
@@ -890,7 +972,8 @@ int orc_backward_pixels(const float *points, int64_t n, int32_t k, const float *
     int nb = (sh_deg + 1) * (sh_deg + 1);
     for (int64_t i = 0; i < n; i++) {
         if (!pr.dsc[i].visible || !cg[i].touched) continue;
-        convex_chain(points + 3 * k * i, k, delta[i], sigma[i], sh + 3 * nb * i, sh_deg, cam, st, &pr.cv[i], &cg[i],
+        convex_chain(points + 3 * k * i, k, delta[i], sigma[i], sh + 3 * nb * i, sh_deg, cam, st, &pr.dsc[i], &pr.cv[i],
+                     &cg[i],
                      dpoints + 3 * k * i, ddelta + i, dsigma + i, dopacity + i, dsh + 3 * nb * i);
     }
     free(cg);
