@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 convex tile rasterizer (3D Convex Splatting, arXiv 2411.14974).
+
+One step = one pass of the whole differentiable rasterizer over one view: per-convex preprocess
+(projection, exact hull, lines, tile ranges, SH colour), depth sort, pair emission, tile sort,
+per-tile blend, per-tile reverse blend and the preprocess backward.  Workload: 1,000,000
+surface-clustered convexes (K = 6 points, SH degree 3, float32) rendered at 1920x1080, one view
+per step cycling over 4 cameras on a sphere of radius 4; the loss cotangent dL/dimage is a fixed
+random image.  Inputs are resident in HBM when the timed region starts and are larger than L2
+(scene 276 MB, screen records 128 MB).
+
+Metric: fwd+bwd pixel throughput (Mpix/s), with the forward-only throughput, the per-stage
+breakdown (CUDA events on the launching stream), the roofline of the dominant kernel, the
+end-to-end number through the host-buffer C-ABI call, and the CPU oracle on a bounded sample.
+
+Multi-GPU: views are independent, so N ranks render N x the views with no data-path collective
+(replicas; weak scaling).  --impl reference times the CPU oracle (binary64 brute force) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd Mpix/s and fwd+bwd ms/iter at 1M convexes 1080p; serving p50/p99 ms"
+WORKLOAD = dict(workload="surface1M_1920x1080", convexes=1_000_000, points_per_convex=6, sh_degree=3,
+                width=1920, height=1080, views_cycled=4, l2="inputs larger than L2 (scene 276 MB)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000, help="convexes (default: the 1M workload)")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and work counts")
+    ap.add_argument("--cpu-pixels", type=int, default=96, help="pixels in the oracle's bounded sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return dict(sm_mhz=med, sm_max_mhz=smax, reasons=sorted(reasons), samples=len(sm))
+
+
+def oracle_sample(sc, cam, npix, seed=0):
+    """The CPU oracle (binary64 brute force over all convexes) on a bounded random pixel sample:
+    forward render plus analytic backward of those pixels.  Returns (seconds, threads)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, cam.width, npix), rng.integers(0, cam.height, npix)], 1).astype(np.int32)
+    st = oracle.settings()
+    t0 = time.perf_counter()
+    oracle.render_pixels(sc, cam, st, pix)
+    oracle.backward_pixels(sc, cam, st, pix, rng.uniform(-1, 1, (npix, 3)))
+    return time.perf_counter() - t0, oracle.num_threads()
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, as it stands, on the host cores (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2411_14974_gb300 import synthetic as syn
+    oracle.build()
+    sc, cams = syn.workload("surface1M_1920x1080", seed=0)
+    if args.n != 1_000_000:
+        sc = sc.subset(range(args.n))
+    cams = cams + syn.sphere_cameras(3, 1920, 1080, 4.0, seed=7)
+    for i in range(args.warmup):
+        oracle_sample(sc, cams[i % len(cams)], args.cpu_pixels, seed=i)
+    tot, thr = 0.0, 1
+    for i in range(args.steps):
+        dt, thr = oracle_sample(sc, cams[i % len(cams)], args.cpu_pixels, seed=100 + i)
+        tot += dt
+    per = tot / max(args.steps, 1)
+    value = args.cpu_pixels / per / 1e6
+    sample = (f"{args.cpu_pixels} random pixels of one 1920x1080 view per step: binary64 forward + analytic "
+              f"backward, brute force over all {sc.n} convexes")
+    line = dict(metric=METRIC, value=value, unit="Mpix/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+                ms_per_step=per * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", config=dict(WORKLOAD), impl="reference",
+                cpu_baseline=dict(value=value, unit="Mpix/s", cores=thr, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="Mpix/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    from paper_2411_14974_gb300 import synthetic as syn
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    sc, cams = syn.workload("surface1M_1920x1080", seed=0)
+    if args.n != 1_000_000:
+        sc = sc.subset(range(args.n))
+    cams = cams + syn.sphere_cameras(3, 1920, 1080, 4.0, seed=7)
+    # replicas: rank r renders views r, r + N, ... of the cycle (weak scaling, no exchange)
+    cams = [cams[(rank + i * ws) % len(cams)] for i in range(len(cams))]
+    H, W = cams[0].height, cams[0].width
+    scene = cs.SceneTensors.from_numpy(sc, dev)
+    dL = torch.as_tensor(np.random.default_rng(1).uniform(-1, 1, (1, 3, H, W)).astype(np.float32), device=dev)
+    grads = dict(points=torch.zeros_like(scene.points), delta=torch.zeros_like(scene.delta),
+                 sigma=torch.zeros_like(scene.sigma), opacity=torch.zeros_like(scene.opacity),
+                 sh=torch.zeros_like(scene.sh))
+    image = torch.empty((1, 3, H, W), device=dev)
+    settings = cs.Settings()
+
+    def step(i):
+        _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
+        cs.backward(st, dL, grads)
+        st.release()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for i in range(args.warmup):
+        step(i)
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    cs.profile_enable(True, local)
+    cs.profile_read(local)
+    barrier()
+    launches0 = cs.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i)
+    e1.record(stream)
+    barrier()
+    launches = cs.launch_count() - launches0
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    stages = cs.profile_read(local)
+    cs.profile_enable(False, local)
+    clk = clocks.stop()
+    ms_step = ms_total / args.steps
+    pixels_per_step = H * W
+    value = ws * pixels_per_step * args.steps / (ms_total / 1e3) / 1e6
+
+    # forward-only throughput (same views)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for i in range(args.steps):
+        cs.forward(scene, [cams[i % len(cams)]], settings, image=image)
+    f1.record(stream)
+    barrier()
+    fwd_ms = max_over_ranks(f0.elapsed_time(f1)) / args.steps
+    fwd_mpix = ws * pixels_per_step / (fwd_ms / 1e3) / 1e6
+
+    breakdown = {k: v[0] / args.steps for k, v in stages.items()}
+    out = dict(metric=METRIC, value=value, unit="Mpix/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
+               ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+               data="synthetic (seeded surface-clustered scene, random cotangent)",
+               config=dict(WORKLOAD, parallelism=f"replicas{ws}"),
+               fwd_mpix_s=fwd_mpix, fwd_ms=fwd_ms, fwd_bwd_ms_per_iter=ms_step,
+               breakdown_ms=breakdown, gpu_launches=launches,
+               clocks=dict(sm_mhz=clk.get("sm_mhz"), sm_max_mhz=clk.get("sm_max_mhz"), reasons=clk.get("reasons")))
+
+    if not args.no_extras and rank == 0:
+        # roofline of the dominant kernel from the instrumented work counts of one step per view
+        dom = max(("blend", "blend_backward"), key=lambda k: breakdown[k])
+        tot = dict(visited=0, lines_visited=0, passed=0, lines_passed=0, contributing=0)
+        for v in range(len(cams)):
+            _, _, st = cs.forward(scene, [cams[v]], settings, keep_state=True, image=image)
+            wc = cs.work_counts(st, dL)["forward" if dom == "blend" else "backward"]
+            st.release()
+            for k in tot:
+                tot[k] += wc[k] / len(cams)
+        # transcendental (MUFU) operations the method needs per evaluated pair: one exp2 per
+        # hull line, the log2, the exp2 of the sigmoid and its reciprocal; the backward adds the
+        # softmax reciprocal and 1/(1 - alpha) per contributing pair
+        mufu = tot["lines_passed"] + 3 * tot["passed"] + (2 * tot["contributing"] if dom != "blend" else 0)
+        # FP32 pipe instructions: per visited pair 2 FMA + 1 max per line; per evaluated pair one
+        # subtract and one add per line plus about 12 for the sigmoid, clamp and compositing
+        fp32 = 3 * tot["lines_visited"] + 2 * tot["lines_passed"] + 12 * tot["passed"]
+        sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.get("sm_max_mhz") or 2070.0
+        mufu_peak = sm * 16 * mhz * 1e6 / 1e9   # Gop/s: 16 MUFU results per clock per SM
+        fp32_peak = sm * 128 * mhz * 1e6 / 1e9  # Ginstr/s: 128 FP32 lanes per clock per SM
+        t = breakdown[dom] / 1e3
+        achieved = mufu / t / 1e9
+        out["roofline"] = dict(kernel=f"k_blend_{'forward' if dom == 'blend' else 'backward'}", bound="alu",
+                               achieved=achieved, peak=mufu_peak, unit="Gop/s (MUFU)", frac=achieved / mufu_peak,
+                               fp32_ginstr_s=fp32 / t / 1e9, fp32_peak_ginstr_s=fp32_peak,
+                               fp32_frac=fp32 / t / 1e9 / fp32_peak, peak_clock_mhz=mhz,
+                               work_per_launch=tot, traffic=None)
+        # end to end through the host-buffer C-ABI call: scene and cotangent uploaded, image and
+        # gradients read back, every step
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory()
+        host_scene = dict(points=pin(sc.points), delta=pin(sc.delta), sigma=pin(sc.sigma), opacity=pin(sc.opacity),
+                          sh=pin(sc.sh))
+        host_dL = dL.cpu().pin_memory()
+        host_img = torch.empty((1, 3, H, W)).pin_memory()
+        host_g = {k: torch.empty(tuple(v.shape)).pin_memory() for k, v in grads.items()}
+        ne = max(3, min(args.steps, 8))
+        cs.step_host(host_scene, sc.sh_degree, [cams[0]], settings, host_dL, host_img, host_g, local)
+        t0 = time.perf_counter()
+        for i in range(ne):
+            cs.step_host(host_scene, sc.sh_degree, [cams[i % len(cams)]], settings, host_dL, host_img, host_g, local)
+        e2e_s = (time.perf_counter() - t0) / ne
+        h2d = sum(v.numel() * 4 for v in host_scene.values()) + host_dL.numel() * 4
+        d2h = host_img.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
+        out["e2e"] = dict(value=pixels_per_step / e2e_s / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
+                          d2h_bytes_per_step=int(d2h), ms_per_step=e2e_s * 1e3)
+        # CPU oracle on a bounded sample of the same workload
+        if ws == 1:
+            import oracle
+            oracle.build()
+            dt, thr = oracle_sample(sc, cams[0], args.cpu_pixels)
+            out["cpu_baseline"] = dict(value=args.cpu_pixels / dt / 1e6, unit="Mpix/s", cores=thr, kind="oracle",
+                                       sample=f"{args.cpu_pixels} random pixels of one view, binary64 forward + "
+                                              f"analytic backward over all {sc.n} convexes ({dt:.1f} s)")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

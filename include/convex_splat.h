@@ -112,7 +112,8 @@ void cs_context_destroy(cs_context *ctx);
 /* Forward render (Sec. 3.2, Eq. 4, 5, S1, S2) of `scene` into n_views views of equal size.
    cams:    host array [n_views]; all views must have the same width and height.
    image:   device [n_views][3][H][W], written.
-   t_final: device [n_views][H][W] final transmittance, written; may be NULL.
+   t_final: device [n_views][H][W] final transmittance, written; may be NULL.  Neither image nor
+            t_final is read again by cs_backward (the state keeps its own copy).
    state_out: if not NULL, receives a new state holding what cs_backward needs (the sorted
             tile-pair lists, per-convex screen records, per-pixel T_final and last contributor);
             release it with cs_state_release.  The scene buffers must stay alive and unchanged
@@ -152,6 +153,45 @@ cs_status cs_state_copy(const cs_fwd_state *state, int32_t which, void *host_dst
 
 /* Numbers of records R (= n_views * N), sorted pairs P and tiles of a forward state. */
 cs_status cs_state_sizes(const cs_fwd_state *state, int64_t *records, int64_t *pairs, int64_t *tiles);
+
+/* One forward (and, if dL_dimage_host is not NULL, backward) with every buffer in HOST memory
+   (preferably pinned): the scene arrays are copied to the device, rendered, and the image and
+   gradients copied back before the call returns.  Same layouts as cs_forward / cs_backward;
+   scene_host holds host pointers.  The gradients are written (not accumulated); any gradient
+   pointer may be NULL.  Device buffers come from the context's pool; the call synchronises. */
+cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_camera *cams, int32_t n_views,
+                       const cs_settings *settings, const float *dL_dimage_host, float *image_host,
+                       float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,
+                       float *dsh_host, void *stream);
+
+/* ---- instrumentation (no counterpart in the paper) ------------------------------------------ */
+typedef enum {
+    CS_STAGE_PREPROCESS = 0,      /* per-convex projection, hull, lines, tile range, colour */
+    CS_STAGE_DEPTH_SORT = 1,      /* radix sort of the records by depth key */
+    CS_STAGE_SCAN_EMIT = 2,       /* tile-count scan, pair-count readback, pair emission */
+    CS_STAGE_TILE_SORT = 3,       /* radix sort of the pairs by tile, tile ranges */
+    CS_STAGE_BLEND = 4,           /* per-tile forward compositing */
+    CS_STAGE_BLEND_BACKWARD = 5,  /* per-tile reverse compositing, per-convex gradient records */
+    CS_STAGE_PREPROCESS_BACKWARD = 6, /* chain to points, delta, sigma, opacity, SH */
+    CS_STAGE_COUNT = 7
+} cs_stage;
+
+/* When on, every stage of every call on this context is bracketed by CUDA events recorded on the
+   stream the stage is launched on. */
+cs_status cs_profile_enable(cs_context *ctx, int32_t on);
+/* Sum of the event-timed milliseconds and number of timed launches per stage since the last read
+   (arrays of CS_STAGE_COUNT); synchronises on the recorded events, then resets the record. */
+cs_status cs_profile_read(cs_context *ctx, double *ms, int64_t *launches);
+/* Total number of kernels this library has launched in the process (monotonic). */
+uint64_t cs_kernel_launch_count(void);
+
+/* Work actually done by the two blend kernels of a forward state, counted by instrumented
+   variants of the kernels (the state's pair lists are re-blended; outputs are unchanged).
+   counts[0..5] forward, counts[6..11] backward: pairs visited, hull lines of the visited pairs,
+   pairs past the line pre-test, hull lines of those, pairs that contribute (alpha >= tau),
+   pixels.  dL_dimage may be NULL (forward counts only). */
+cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *state, const float *dL_dimage, uint64_t *counts,
+                         void *stream);
 
 #ifdef __cplusplus
 }

@@ -38,7 +38,15 @@ _PROTOTYPES = {
     "cs_state_copy": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_state_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64)]),
+    "cs_step_host": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera), ctypes.c_int32,
+                                    ctypes.POINTER(CsSettings), _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cs_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cs_profile_read": (ctypes.c_int, [_P, _P, _P]),
+    "cs_kernel_launch_count": (ctypes.c_uint64, []),
+    "cs_work_counts": (ctypes.c_int, [_P, _P, _P, _P, _P]),
 }
+
+STAGES = ("preprocess", "depth_sort", "scan_emit", "tile_sort", "blend", "blend_backward", "preprocess_backward")
 
 _lib = None
 

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -31,6 +32,76 @@ cs_status cs::fail_cuda(cudaError_t e, const char *what) {
 }
 
 extern "C" const char *cs_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------------------------
+// instrumentation: launch counter and per-stage events
+// ---------------------------------------------------------------------------------------------
+static std::atomic<uint64_t> g_launches{0};
+void cs::count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+extern "C" uint64_t cs_kernel_launch_count(void) { return g_launches.load(); }
+
+static cudaEvent_t take_event(cs_context *ctx) {
+    cudaEvent_t e = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->prof_mu);
+        if (!ctx->free_events.empty()) {
+            e = ctx->free_events.back();
+            ctx->free_events.pop_back();
+        }
+    }
+    if (!e && cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+    return e;
+}
+
+cs::StageTimer::StageTimer(cs_context *ctx, int stage, cudaStream_t s) : ctx_(ctx), stage_(stage), s_(s) {
+    if (ctx_ && ctx_->profiling) {
+        a_ = take_event(ctx_);
+        if (a_) cudaEventRecord(a_, s_);
+    }
+}
+
+cs::StageTimer::~StageTimer() {
+    if (!a_) return;
+    cudaEvent_t b = take_event(ctx_);
+    if (!b) return;
+    cudaEventRecord(b, s_);
+    std::lock_guard<std::mutex> lk(ctx_->prof_mu);
+    ctx_->prof.push_back({stage_, a_, b});
+}
+
+extern "C" cs_status cs_profile_enable(cs_context *ctx, int32_t on) {
+    if (!ctx) return fail(CS_ERR_ARG, "context is NULL");
+    ctx->profiling = on != 0;
+    return CS_OK;
+}
+
+extern "C" cs_status cs_profile_read(cs_context *ctx, double *ms, int64_t *launches) {
+    if (!ctx) return fail(CS_ERR_ARG, "context is NULL");
+    std::vector<cs_context::StageRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(ctx->prof_mu);
+        recs.swap(ctx->prof);
+    }
+    for (int i = 0; i < CS_STAGE_COUNT; ++i) {
+        if (ms) ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    cs_status st = CS_OK;
+    for (auto &r : recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && st == CS_OK) st = fail_cuda(e, "profile events");
+        if (r.stage >= 0 && r.stage < CS_STAGE_COUNT) {
+            if (ms) ms[r.stage] += t;
+            if (launches) launches[r.stage] += 1;
+        }
+        std::lock_guard<std::mutex> lk(ctx->prof_mu);
+        ctx->free_events.push_back(r.a);
+        ctx->free_events.push_back(r.b);
+    }
+    return st;
+}
 
 extern "C" void cs_default_settings(cs_settings *s) {
     if (!s) return;
@@ -97,6 +168,11 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
     if (ctx->host_total) cudaFreeHost(ctx->host_total);
     cudaMemPoolTrimTo(ctx->pool, 0);
     cudaMemPoolDestroy(ctx->pool);
@@ -247,23 +323,24 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     CS_TRY(pool_alloc(ctx, (void **)&s->ranges, (size_t)tiles * 8, stream), "alloc ranges");
     CS_TRY(pool_alloc(ctx, (void **)&s->n_last, pix_total * 4, stream), "alloc n_last");
     {
-        bool need_t = false;
-        for (int v = 0; v < V; ++v) need_t |= s->views[v].t_final == nullptr;
-        if (need_t) {
-            CS_TRY(pool_alloc(ctx, (void **)&s->t_final_own, pix_total * 4, stream), "alloc t_final");
-        }
+        // the state owns T_final (the backward needs it after the caller's buffers may be gone);
+        // callers that asked for it get a copy once the blend has run
+        CS_TRY(pool_alloc(ctx, (void **)&s->t_final_own, pix_total * 4, stream), "alloc t_final");
+        s->user_t_final.assign(V, nullptr);
         size_t off = 0;
         for (int v = 0; v < V; ++v) {
             ViewDesc &vd = s->views[v];
             const size_t np = (size_t)vd.width * vd.height;
             vd.n_last = s->n_last + off;
-            if (!vd.t_final) vd.t_final = s->t_final_own + off;
+            s->user_t_final[v] = vd.t_final;
+            vd.t_final = s->t_final_own + off;
             off += np;
         }
     }
     CS_TRY(cudaMemcpyAsync(s->views_dev, s->views.data(), sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, stream),
            "copy views");
     {
+        StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
         PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
     }
@@ -278,14 +355,18 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words(R) * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_words * 8, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&total, 16, stream), "alloc");
-        if (R > 0) {
-            CS_TRY(cudaMemcpyAsync(sort_keys_a, s->depth_keys, (size_t)R * 4, cudaMemcpyDeviceToDevice, stream),
-                   "copy keys");
+        {
+            StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
+            if (R > 0) {
+                CS_TRY(cudaMemcpyAsync(sort_keys_a, s->depth_keys, (size_t)R * 4, cudaMemcpyDeviceToDevice, stream),
+                       "copy keys");
+            }
+            CS_TRY(launch_iota(sort_vals_a, R, stream), "iota");
+            CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, 32, radix_tmp, scan_tmp,
+                                    &in_b, stream),
+                   "depth sort");
         }
-        CS_TRY(launch_iota(sort_vals_a, R, stream), "iota");
-        CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, 32, radix_tmp, scan_tmp, &in_b,
-                                stream),
-               "depth sort");
+        StageTimer tm(ctx, CS_STAGE_SCAN_EMIT, stream);
         uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;
         CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, total, scan_tmp, stream), "scan");
         CS_TRY(cudaMemcpyAsync(ctx->host_total, total, 8, cudaMemcpyDeviceToHost, stream), "read pair count");
@@ -306,6 +387,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     }
     // stable sort of the pairs by tile
     {
+        StageTimer tm(ctx, CS_STAGE_TILE_SORT, stream);
         pool_free(radix_tmp, stream);
         pool_free(scan_tmp, stream);
         radix_tmp = nullptr;
@@ -323,8 +405,17 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->ranges, tiles, stream), "tile ranges");
     }
     {
+        StageTimer tm(ctx, CS_STAGE_BLEND, stream);
         BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, tiles};
         CS_TRY(launch_blend_forward(a, stream), "blend");
+    }
+    for (int v = 0; v < V; ++v) {
+        const ViewDesc &vd = s->views[v];
+        if (s->user_t_final[v]) {
+            CS_TRY(cudaMemcpyAsync(s->user_t_final[v], vd.t_final, (size_t)vd.width * vd.height * 4,
+                                   cudaMemcpyDeviceToDevice, stream),
+                   "copy t_final");
+        }
     }
 cleanup:
     pool_free(sort_keys_a, stream);
@@ -411,11 +502,13 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         if (e != cudaSuccess) return fail_cuda(e, "alloc gradient records");
         e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e == cudaSuccess) {
+            StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
             BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, s->n_tiles};
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }
         if (e == cudaSuccess) {
+            StageTimer tm(ctx, CS_STAGE_PREPROCESS_BACKWARD, stream);
             PreprocessGrads g{dpoints, ddelta, dsigma, dopacity, dsh};
             e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->st, s->records, s->counts, grads, g,
                                            V > 1, stream);
@@ -478,5 +571,83 @@ extern "C" cs_status cs_state_copy(const cs_fwd_state *s, int32_t which, void *h
         e = cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail_cuda(e, "copy");
     }
+    return CS_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// host-buffer step and work counters
+// ---------------------------------------------------------------------------------------------
+extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_camera *cams, int32_t n_views,
+                                  const cs_settings *settings, const float *dL_host, float *image_host,
+                                  float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,
+                                  float *dsh_host, void *stream_ptr) {
+    if (!ctx) return fail(CS_ERR_ARG, "context is NULL");
+    cs_status st;
+    if ((st = check_scene(sh)) != CS_OK) return st;
+    if (!cams || n_views <= 0 || !image_host) return fail(CS_ERR_ARG, "cameras and image are required");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    const int64_t n = sh->n;
+    const int nb = (sh->sh_degree + 1) * (sh->sh_degree + 1);
+    const size_t b_pts = (size_t)n * sh->k * 3 * 4, b_one = (size_t)n * 4, b_sh = (size_t)n * nb * 3 * 4;
+    const size_t b_img = (size_t)n_views * 3 * cams[0].width * cams[0].height * 4;
+    float *d[12] = {};
+    const size_t sizes[12] = {b_pts, b_one, b_one, b_one, b_sh, b_img, b_img, b_pts, b_one, b_one, b_one, b_sh};
+    const bool bwd = dL_host != nullptr;
+    const int nbuf = bwd ? 12 : 6;
+    cs_fwd_state *state = nullptr;
+    cs_status code = CS_OK;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nbuf && e == cudaSuccess; ++i) e = pool_alloc(ctx, (void **)&d[i], sizes[i], stream);
+    const void *srcs[5] = {sh->points, sh->delta, sh->sigma, sh->opacity, sh->sh};
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i)
+        if (sizes[i]) e = cudaMemcpyAsync(d[i], srcs[i], sizes[i], cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && bwd) e = cudaMemcpyAsync(d[6], dL_host, b_img, cudaMemcpyHostToDevice, stream);
+    for (int i = 7; i < 12 && e == cudaSuccess && bwd; ++i) e = cudaMemsetAsync(d[i], 0, sizes[i], stream);
+    if (e != cudaSuccess) code = fail_cuda(e, "cs_step_host upload");
+    if (code == CS_OK) {
+        cs_scene dev = *sh;
+        dev.points = d[0]; dev.delta = d[1]; dev.sigma = d[2]; dev.opacity = d[3]; dev.sh = d[4];
+        code = cs_forward(ctx, &dev, cams, n_views, settings, d[5], nullptr, bwd ? &state : nullptr, stream_ptr);
+        if (code == CS_OK && bwd) code = cs_backward(ctx, state, d[6], d[7], d[8], d[9], d[10], d[11], stream_ptr);
+    }
+    if (code == CS_OK) {
+        e = cudaMemcpyAsync(image_host, d[5], b_img, cudaMemcpyDeviceToHost, stream);
+        float *outs[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
+        for (int i = 0; i < 5 && e == cudaSuccess && bwd; ++i)
+            if (outs[i] && sizes[7 + i]) e = cudaMemcpyAsync(outs[i], d[7 + i], sizes[7 + i], cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) code = fail_cuda(e, "cs_step_host download");
+    }
+    if (state) state_free(state);
+    for (int i = 0; i < nbuf; ++i) pool_free(d[i], stream);
+    return code;
+}
+
+extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, uint64_t *counts,
+                                    void *stream_ptr) {
+    if (!ctx || !s || !counts) return fail(CS_ERR_ARG, "context, state and counts are required");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    unsigned long long *dc = nullptr;
+    float4 *grads = nullptr;
+    cudaError_t e = pool_alloc(ctx, (void **)&dc, 12 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 12 * sizeof(unsigned long long), stream);
+    const int V = (int)s->views.size();
+    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, s->n_tiles};
+    if (e == cudaSuccess) e = launch_blend_forward(a, stream, dc);
+    if (e == cudaSuccess && dL_dimage && s->n_records) {
+        e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
+        const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
+        if (e == cudaSuccess) e = launch_blend_backward(a, dL_dimage, stride, grads, stream, dc + 6);
+    }
+    unsigned long long host[12] = {};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, dc, sizeof host, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    pool_free(grads, stream);
+    pool_free(dc, stream);
+    if (e != cudaSuccess) return fail_cuda(e, "cs_work_counts");
+    for (int i = 0; i < 12; ++i) counts[i] = host[i];
     return CS_OK;
 }

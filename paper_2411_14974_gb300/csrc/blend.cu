@@ -84,14 +84,15 @@ __device__ __forceinline__ void stage_record(float4 *dst, const float4 *__restri
     }
 }
 
-// Evaluate one (pixel, convex) pair.  Returns false when the pair adds nothing (alpha < tau).
+// Terms of one (pixel, convex) pair kept for the backward.
 struct PairTerms {
     float alpha, I, z, oI, phi2, S;
     float e[KMAX];
 };
 
-__device__ __forceinline__ bool eval_pair(const float4 *__restrict__ rec, float lx, float ly, const Settings &st,
-                                          PairTerms &p) {
+// returns 0 when the line pre-test rejects the pair, 1 when alpha < tau, 2 when it contributes
+__device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float lx, float ly, const Settings &st,
+                                         PairTerms &p) {
     const float4 h0 = rec[0];
     const int T = __float_as_int(h0.w);
     float s[KMAX];
@@ -104,7 +105,7 @@ __device__ __forceinline__ bool eval_pair(const float4 *__restrict__ rec, float 
             m = fmaxf(m, s[t]);
         }
     }
-    if (m > h0.y) return false;
+    if (m > h0.y) return 0;
     float S = 0.f;
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
@@ -119,7 +120,20 @@ __device__ __forceinline__ bool eval_pair(const float4 *__restrict__ rec, float 
     p.I = rcp(1.0f + p.z);
     p.oI = h0.z * p.I;
     p.alpha = fminf(st.alpha_max, p.oI);
-    return p.alpha >= st.tau;
+    return p.alpha >= st.tau ? 2 : 1;
+}
+
+// work counters of the instrumented kernel variants: pairs visited, their hull lines, pairs past
+// the line pre-test, their hull lines, contributing pairs, pixels
+constexpr int NCOUNT = 6;
+__device__ __forceinline__ void flush_counts(unsigned long long *dst, const unsigned long long (&c)[NCOUNT]) {
+#pragma unroll
+    for (int q = 0; q < NCOUNT; ++q) {
+        unsigned long long x = c[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(dst + q, x);
+    }
 }
 
 __device__ __forceinline__ int find_view(const ViewDesc *__restrict__ views, int n_views, uint32_t g) {
@@ -134,7 +148,8 @@ __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
     ly = (w >> 1) * 4 + (lane >> 3);
 }
 
-__global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a) {
+template <bool COUNT>
+__global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[BATCH * SREC];
     const uint32_t g = blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
@@ -151,6 +166,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a) {
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !inside;
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
     for (uint32_t base = range.x; base < range.y; base += BATCH) {
         if (__syncthreads_and(done)) break;
         const uint32_t nb = min((uint32_t)BATCH, range.y - base);
@@ -162,7 +178,18 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a) {
             for (uint32_t j = 0; j < nb; ++j) {
                 PairTerms p;
                 const float4 *rec = srec + j * SREC;
-                if (!eval_pair(rec, lx, ly, st, p)) continue;
+                const int code = eval_pair(rec, lx, ly, st, p);
+                if (COUNT) {
+                    const unsigned T = (unsigned)__float_as_int(rec[0].w);
+                    cnt[0]++;
+                    cnt[1] += T;
+                    if (code) {
+                        cnt[2]++;
+                        cnt[3] += T;
+                    }
+                    if (code == 2) cnt[4]++;
+                }
+                if (code != 2) continue;
                 const float4 c = rec[1];
                 const float wgt = p.alpha * T;
                 C0 = fmaf(wgt, c.x, C0);
@@ -185,6 +212,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a) {
         if (vd.t_final) vd.t_final[pix] = T;
         vd.n_last[pix] = last;
     }
+    if (COUNT) flush_counts(counts, cnt);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -193,8 +221,10 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
-                                                                  int64_t image_stride, float4 *__restrict__ grads) {
+                                                                  int64_t image_stride, float4 *__restrict__ grads,
+                                                                  unsigned long long *counts) {
     __shared__ float4 srec[BATCH * SREC];
     __shared__ uint32_t s_max_last[BLEND_THREADS / 32];
     const uint32_t g = blockIdx.x;
@@ -224,6 +254,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
     }
     // colour seen behind the current pair, T_after * (its colour) summed from the back
     float S0 = Tc * st.bg[0], S1 = Tc * st.bg[1], S2 = Tc * st.bg[2];
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
     uint32_t wl = last;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
@@ -245,7 +276,18 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
             const float4 *rec = srec + j * SREC;
             const uint32_t idx = start + (uint32_t)j;
             PairTerms p;
-            bool on = idx < last && eval_pair(rec, lx, ly, st, p);
+            const int code = idx < last ? eval_pair(rec, lx, ly, st, p) : -1;
+            const bool on = code == 2;
+            if (COUNT && code >= 0) {
+                const unsigned T = (unsigned)__float_as_int(rec[0].w);
+                cnt[0]++;
+                cnt[1] += T;
+                if (code) {
+                    cnt[2]++;
+                    cnt[3] += T;
+                }
+                if (on) cnt[4]++;
+            }
             if (!__any_sync(0xffffffffu, on)) continue;
             const float4 h0 = rec[0];
             const int T = __float_as_int(h0.w);
@@ -331,20 +373,27 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
         }
         end = start;
     }
+    if (COUNT) flush_counts(counts, cnt);
 }
 
 }  // namespace
 
-cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s) {
+cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
-    k_blend_forward<<<a.n_tiles, BLEND_THREADS, 0, s>>>(a);
+    if (counts) k_blend_forward<true><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, counts);
+    else k_blend_forward<false><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, nullptr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,
-                                  float4 *grad_records, cudaStream_t s) {
+                                  float4 *grad_records, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
-    k_blend_backward<<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records);
+    if (counts)
+        k_blend_backward<true><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
+    else
+        k_blend_backward<false><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
+    count_launches(1);
     return cudaGetLastError();
 }
 

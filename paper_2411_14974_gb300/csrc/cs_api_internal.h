@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <vector>
 
 #include "cs_common.cuh"
@@ -12,6 +13,15 @@ struct cs_context {
     int sm_count = 0;
     cudaMemPool_t pool = nullptr;             // stream-ordered pool for every transient buffer
     unsigned long long *host_total = nullptr; // pinned readback slot for the pair count
+    // stage profiling: events recorded on the launching stream around every stage
+    bool profiling = false;
+    struct StageRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::mutex prof_mu;
+    std::vector<StageRec> prof;
+    std::vector<cudaEvent_t> free_events;
 };
 
 struct cs_fwd_state {
@@ -32,7 +42,8 @@ struct cs_fwd_state {
     uint32_t *pair_keys = nullptr, *pair_vals = nullptr;
     uint2 *ranges = nullptr;
     uint32_t *n_last = nullptr;
-    float *t_final_own = nullptr;
+    float *t_final_own = nullptr;          // [pixels of all views], read by the backward
+    std::vector<float *> user_t_final;     // caller's T_final buffers (copied to after the blend)
 };
 
 namespace cs {
@@ -47,4 +58,17 @@ void fill_view(ViewDesc &vd, const cs_camera &c);
 Settings to_settings(const cs_settings &s);
 cs_status run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream);
 void state_free(cs_fwd_state *s);
+
+// brackets a stage with events when the context is profiling
+class StageTimer {
+  public:
+    StageTimer(cs_context *ctx, int stage, cudaStream_t s);
+    ~StageTimer();
+
+  private:
+    cs_context *ctx_;
+    int stage_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr;
+};
 }  // namespace cs

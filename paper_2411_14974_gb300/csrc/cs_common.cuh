@@ -104,8 +104,12 @@ struct BlendArgs {
     Settings st;
     uint32_t n_tiles;
 };
-cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s);
+// counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
+cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,
-                                  float4 *grad_records, cudaStream_t s);
+                                  float4 *grad_records, cudaStream_t s, unsigned long long *counts = nullptr);
+
+// process-wide count of kernel launches made by the library
+void count_launches(int n);
 
 }  // namespace cs

@@ -616,6 +616,7 @@ cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *, int n
         case 8: k_preprocess<8><<<grid, PRE_THREADS, 0, s>>>(views_dev, st, out); break;
         default: return cudaErrorInvalidValue;
     }
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -637,6 +638,7 @@ cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, i
         default: return cudaErrorInvalidValue;
     }
 #undef CS_PRE_BWD
+    count_launches(1);
     return cudaGetLastError();
 }
 

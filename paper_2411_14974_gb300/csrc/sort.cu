@@ -247,6 +247,7 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather, ui
     k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp);
     k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(tmp, nb, total_dev);
     k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out);
+    count_launches(3);
     return cudaGetLastError();
 }
 
@@ -273,6 +274,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
         cudaError_t e = launch_exclusive_scan(hist, nullptr, offs, nh, nullptr, scan_tmp, s);
         if (e != cudaSuccess) return e;
         k_radix_scatter<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, vin, n, shift, w, offs, nb, kout, vout);
+        count_launches(2);
         shift += w;
         uint32_t *t;
         t = kin; kin = kout; kout = t;
@@ -285,6 +287,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
 cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -294,6 +297,7 @@ cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint
     if (n_records <= 0) return cudaSuccess;
     k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
                                                                rects, n_records, pair_keys, pair_vals);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -302,6 +306,7 @@ cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, uint2
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
     k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, ranges);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -231,3 +231,61 @@ def render(points, delta, sigma, opacity, sh, cams, settings: Optional[Settings]
 
     delta, sigma, opacity are activated values (> 0, > 0, in (0, 1])."""
     return _Render.apply(points, delta, sigma, opacity, sh, list(cams), settings or Settings())
+
+
+# ---- instrumentation and host-buffer entry points ---------------------------------------------
+def profile_enable(on: bool = True, device: int = 0):
+    """Bracket every stage of every call with CUDA events on the launching stream."""
+    B.check(B.lib().cs_profile_enable(Context.get(device).handle, int(bool(on))), "cs_profile_enable")
+
+
+def profile_read(device: int = 0) -> dict:
+    """{stage: (total ms, timed launches)} since the last read."""
+    n = len(B.STAGES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    B.check(B.lib().cs_profile_read(Context.get(device).handle, ms, cnt), "cs_profile_read")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(B.STAGES)}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(B.lib().cs_kernel_launch_count())
+
+
+WORK_FIELDS = ("visited", "lines_visited", "passed", "lines_passed", "contributing", "pixels")
+
+
+def work_counts(state: State, dL_dimage: Optional[torch.Tensor] = None) -> dict:
+    """Work done by the forward (and backward) blend of a state, from instrumented kernels."""
+    out = (ctypes.c_uint64 * 12)()
+    g = dL_dimage.contiguous() if dL_dimage is not None else None
+    B.check(B.lib().cs_work_counts(state.ctx.handle, state.handle, g.data_ptr() if g is not None else None, out,
+                                   _stream_ptr(state.scene.points.device)), "cs_work_counts")
+    fwd = {k: int(out[i]) for i, k in enumerate(WORK_FIELDS)}
+    bwd = {k: int(out[6 + i]) for i, k in enumerate(WORK_FIELDS)}
+    return dict(forward=fwd, backward=bwd)
+
+
+def step_host(scene_host: dict, sh_degree: int, cams: Sequence, settings: Optional[Settings], dL_host, image_host,
+              grads_host: Optional[dict] = None, device: int = 0):
+    """cs_step_host: one forward (+ backward when dL_host is given) with every buffer in host memory.
+
+    scene_host: dict of contiguous float32 CPU tensors (points, delta, sigma, opacity, sh), ideally
+    pinned; image_host / dL_host / grads_host likewise."""
+    ctx = Context.get(device)
+    sc = B.CsScene()
+    for name in ("points", "delta", "sigma", "opacity", "sh"):
+        t = scene_host[name]
+        setattr(sc, name, t.data_ptr() if t.numel() else None)
+    sc.n = int(scene_host["points"].shape[0])
+    sc.k = int(scene_host["points"].shape[1])
+    sc.sh_degree = int(sh_degree)
+    s = (settings or Settings()).struct()
+    g = grads_host or {}
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    code = B.lib().cs_step_host(ctx.handle, ctypes.byref(sc), cameras_array(cams), len(cams), ctypes.byref(s),
+                                ptr(dL_host), image_host.data_ptr(), ptr(g.get("points")), ptr(g.get("delta")),
+                                ptr(g.get("sigma")), ptr(g.get("opacity")), ptr(g.get("sh")),
+                                _stream_ptr(torch.device("cuda", device)))
+    B.check(code, "cs_step_host")

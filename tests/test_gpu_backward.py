@@ -170,3 +170,25 @@ def test_gradient_against_finite_differences():
         assert abs(a - rich) <= 2e-3 * abs(rich) + 1e-4 * gmax + 0.05 * abs(d1 - d2), (field, idx, a, rich, d1, d2)
         checked += 1
     assert checked >= 40
+
+
+def test_autograd_render_matches_direct_backward_after_buffers_are_freed():
+    """torch.autograd path (render -> loss.backward) equals the direct C-ABI backward, even when the
+    forward's image / T_final tensors are released and their memory reused before the backward."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = _blob(4, deg=1)
+    cam = syn.blob_camera(64, 48)
+    G = np.random.default_rng(9).uniform(-1, 1, (1, 3, 48, 64))
+    want, _ = gpu_grads(sc, [cam], G)
+    t = cs.SceneTensors.from_numpy(sc, torch.device("cuda:0"))
+    params = [getattr(t, f).clone().requires_grad_(True) for f in FIELDS]
+    img = cs.render(*params, [cam])
+    loss = (img * torch.as_tensor(G, dtype=torch.float32, device="cuda:0")).sum()
+    junk = [torch.full((1 << 20,), float("nan"), device="cuda:0") for _ in range(8)]  # reuse freed memory
+    loss.backward()
+    del junk
+    for f, p in zip(FIELDS, params):
+        got = p.grad.detach().cpu().numpy().astype(np.float64)
+        scale = np.abs(want[f]).max() + 1e-30
+        assert np.abs(got - want[f]).max() <= 1e-5 * scale, f
