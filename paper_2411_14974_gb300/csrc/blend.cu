@@ -14,8 +14,10 @@
 //
 // The backward walks each tile's list in reverse from the last contributor of each pixel,
 // recovering T before a pair as T_after / (1 - alpha), and accumulates d(loss)/d(record) per
-// convex: per-pixel terms are summed across the warp with shuffles and added to the convex's
-// gradient record with one vector atomic per four words per warp.
+// convex: the 29 per-pixel terms are summed across the warp by a reduce-scatter (31 shuffles,
+// lane l ends with word l) and added to the convex's gradient record by one coalesced atomic
+// instruction per warp.  A staged record also carries an 8-bit mask of the warps whose 8x4 pixel
+// block can pass the line pre-test at all; the other warps skip it without evaluating.
 #include "cs_common.cuh"
 
 namespace cs {
@@ -26,7 +28,8 @@ constexpr int BATCH = 128;  // records staged per round
 constexpr int SREC = 10;    // float4 per staged record
 // staged record: [0] = (sigma', prefilter bound, o, T)   [1] = (r, g, b, -)
 //                [2 + t] = (A_t, B_t, C_t relative to the tile origin, aux)
-//                aux of line 0/1/2 = tile origin minus anchor (x, y), record index (backward)
+//                aux of line 0/1/2 = tile origin minus anchor (x, y), record index (backward);
+//                [1].w = bit w set when warp w may see alpha >= tau (warp-level cull)
 constexpr float LN2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float ex2(float x) {
@@ -72,16 +75,28 @@ __device__ __forceinline__ void stage_record(float4 *dst, const float4 *__restri
             bound = b + fabsf(b) * 0x1p-10f + 0x1p-10f;
         }
     }
-    dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
-    dst[1] = make_float4(h1.x, h1.y, h1.z, 0.f);
+    // warp cull: warp w covers pixel centres lx in [8(w&1) + .5, 8(w&1) + 7.5], ly in
+    // [4(w>>1) + .5, 4(w>>1) + 3.5]; if for some line the smallest value over that block exceeds
+    // the bound (with a margin covering the per-pixel rounding), no pixel of the warp passes
+    uint32_t wmask = 0xffu;
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
         if (t < T) {
             const float A = L[3 * t], B = L[3 * t + 1], C = L[3 * t + 2];
+            const float Cp = fmaf(A, offx, fmaf(B, offy, C));
             const float aux = t == 0 ? offx : (t == 1 ? offy : __uint_as_float(r));
-            dst[2 + t] = make_float4(A, B, fmaf(A, offx, fmaf(B, offy, C)), aux);
+            dst[2 + t] = make_float4(A, B, Cp, aux);
+            const float margin = (fabsf(Cp) + 16.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
+#pragma unroll
+            for (int w = 0; w < BLEND_THREADS / 32; ++w) {
+                const float x0 = (float)((w & 1) * 8) + 0.5f, y0 = (float)((w >> 1) * 4) + 0.5f;
+                const float mx = fminf(A * x0, A * (x0 + 7.f)), my = fminf(B * y0, B * (y0 + 3.f));
+                if (Cp + mx + my > bound + margin) wmask &= ~(1u << w);
+            }
         }
     }
+    dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
+    dst[1] = make_float4(h1.x, h1.y, h1.z, __uint_as_float(wmask));
 }
 
 // Terms of one (pixel, convex) pair kept for the backward.
@@ -175,9 +190,11 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
                          (float)(tx * TILE), (float)(ty * TILE), st);
         __syncthreads();
         if (!done) {
+            const uint32_t wbit = 1u << (threadIdx.x >> 5);
             for (uint32_t j = 0; j < nb; ++j) {
                 PairTerms p;
                 const float4 *rec = srec + j * SREC;
+                if (!(__float_as_uint(rec[1].w) & wbit)) continue;  // warp-uniform
                 const int code = eval_pair(rec, lx, ly, st, p);
                 if (COUNT) {
                     const unsigned T = (unsigned)__float_as_int(rec[0].w);
@@ -213,12 +230,6 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
         vd.n_last[pix] = last;
     }
     if (COUNT) flush_counts(counts, cnt);
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 template <bool COUNT>
@@ -272,8 +283,10 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
             stage_record(srec + threadIdx.x * SREC, a.records, a.pair_vals[start + threadIdx.x],
                          (float)(tx * TILE), (float)(ty * TILE), st);
         __syncthreads();
+        const uint32_t wbit = 1u << (threadIdx.x >> 5);
         for (int j = (int)nb - 1; j >= 0; --j) {
             const float4 *rec = srec + j * SREC;
+            if (!(__float_as_uint(rec[1].w) & wbit)) continue;  // warp-uniform
             const uint32_t idx = start + (uint32_t)j;
             PairTerms p;
             const int code = idx < last ? eval_pair(rec, lx, ly, st, p) : -1;
@@ -291,85 +304,63 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
             if (!__any_sync(0xffffffffu, on)) continue;
             const float4 h0 = rec[0];
             const int T = __float_as_int(h0.w);
-            float gs[KMAX], gx[KMAX], gy[KMAX];
-            float dsig = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+            // per-pixel terms in gradient-record word order: 3t+0 = g_t lx, 3t+1 = g_t ly,
+            // 3t+2 = g_t, 24 dsigma', 25 dopacity, 26..28 dcolour
+            float v[32];
 #pragma unroll
-            for (int t = 0; t < KMAX; ++t) gs[t] = gx[t] = gy[t] = 0.f;
+            for (int q = 0; q < 32; ++q) v[q] = 0.f;
             if (on) {
                 const float4 c = rec[1];
                 const float om = 1.0f - p.alpha;
-                const float Tn = Tc / om;  // transmittance in front of this pair
-                const float dalpha = G0 * (Tn * c.x - S0 / om) + G1 * (Tn * c.y - S1 / om) + G2 * (Tn * c.z - S2 / om);
+                const float inv = __frcp_rn(om);
+                const float Tn = Tc * inv;  // transmittance in front of this pair
+                const float dalpha = G0 * (Tn * c.x - S0 * inv) + G1 * (Tn * c.y - S1 * inv) + G2 * (Tn * c.z - S2 * inv);
                 const float ta = Tn * p.alpha;
-                dr = G0 * ta;
-                dg = G1 * ta;
-                db = G2 * ta;
+                v[G_RGB] = G0 * ta;
+                v[G_RGB + 1] = G1 * ta;
+                v[G_RGB + 2] = G2 * ta;
                 S0 = fmaf(ta, c.x, S0);
                 S1 = fmaf(ta, c.y, S1);
                 S2 = fmaf(ta, c.z, S2);
                 Tc = Tn;
                 if (p.oI < st.alpha_max) {
-                    dop = dalpha * p.I;
+                    v[G_OPA] = dalpha * p.I;
                     const float dI = dalpha * h0.z;
                     // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
                     const float dx = -dI * LN2 * p.z * p.I * p.I;
-                    dsig = dx * p.phi2;
-                    const float dphi2 = dx * h0.x;
-                    const float inv = rcp(p.S);
+                    v[G_SIG] = dx * p.phi2;
+                    const float dphi2 = dx * h0.x * rcp(p.S);
 #pragma unroll
                     for (int t = 0; t < KMAX; ++t) {
                         if (t < T) {
-                            const float gt = dphi2 * p.e[t] * inv;
-                            gs[t] = gt;
-                            gx[t] = gt * lx;
-                            gy[t] = gt * ly;
+                            const float gt = dphi2 * p.e[t];
+                            v[3 * t] = gt * lx;
+                            v[3 * t + 1] = gt * ly;
+                            v[3 * t + 2] = gt;
                         }
                     }
                 }
             }
-            // warp sums, then one lane adds them to the convex's gradient record
-            dsig = warp_sum(dsig);
-            dop = warp_sum(dop);
-            dr = warp_sum(dr);
-            dg = warp_sum(dg);
-            db = warp_sum(db);
+            // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v[l]
 #pragma unroll
-            for (int t = 0; t < KMAX; ++t) {
-                if (t < T) {
-                    gs[t] = warp_sum(gs[t]);
-                    gx[t] = warp_sum(gx[t]);
-                    gy[t] = warp_sum(gy[t]);
+            for (int h = 16; h >= 1; h >>= 1) {
+                const bool upper = (lane & h) != 0;
+#pragma unroll
+                for (int q = 0; q < h; ++q) {
+                    const float send = upper ? v[q] : v[q + h];
+                    const float keep = upper ? v[q + h] : v[q];
+                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
                 }
             }
-            if (lane == 0) {
-                const float offx = rec[2].w, offy = rec[3].w;
-                const uint32_t r = __float_as_uint(rec[4].w);
-                float w[GRAD_WORDS];
-#pragma unroll
-                for (int q = 0; q < GRAD_WORDS; ++q) w[q] = 0.f;
-#pragma unroll
-                for (int t = 0; t < KMAX; ++t) {
-                    if (t < T) {
-                        // s = A (lx + offx) + B (ly + offy) + C
-                        w[3 * t] = gx[t] + offx * gs[t];
-                        w[3 * t + 1] = gy[t] + offy * gs[t];
-                        w[3 * t + 2] = gs[t];
-                    }
-                }
-                w[G_SIG] = dsig;
-                w[G_OPA] = dop;
-                w[G_RGB] = dr;
-                w[G_RGB + 1] = dg;
-                w[G_RGB + 2] = db;
-                float4 *dst = grads + (size_t)r * (GRAD_WORDS / 4);
-#pragma unroll
-                for (int q = 0; q < GRAD_WORDS / 4; ++q) {
-                    if (4 * q < 3 * T || q >= 6) {
-                        if (q == 7 && w[28] == 0.f) continue;
-                        atomicAdd(dst + q, make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]));
-                    }
-                }
-            }
+            float word = v[0];
+            // s = A (lx + offx) + B (ly + offy) + C: dA = sum(g lx) + offx sum(g), dB likewise
+            const float g2 = __shfl_down_sync(0xffffffffu, word, 2);
+            const float g1 = __shfl_down_sync(0xffffffffu, word, 1);
+            const int slot = lane < 24 ? lane % 3 : 3;
+            if (slot == 0) word = fmaf(rec[2].w, g2, word);
+            else if (slot == 1) word = fmaf(rec[3].w, g1, word);
+            const uint32_t r = __float_as_uint(rec[4].w);
+            if (lane < 29 && word != 0.f) atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
         }
         end = start;
     }
