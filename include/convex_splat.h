@@ -164,6 +164,31 @@ cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_cam
                        float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,
                        float *dsh_host, void *stream);
 
+/* ---- forward that allocates nothing (no counterpart in the paper) ---------------------------
+   For callers that cannot allocate device memory at the point where they render: an engine that
+   owns every byte of device memory through its own arena (a hidden cudaMalloc would escape its
+   accounting), a real-time loop that must not enter the driver's allocator (it can block or
+   synchronise), or a plugin that may only allocate while it is being set up.
+   cs_forward_static renders ONE view (the same computation as cs_forward with n_views = 1) and
+   takes every transient buffer from a fixed device array of CS_STATIC_SCRATCH_BYTES declared at
+   file scope in the library; it calls no cudaMalloc, cudaFree or other allocating routine.
+   scene: device pointers as for cs_forward.  image [3][H][W] and t_final [H][W]: device, written,
+   both required.  Limits: n <= CS_STATIC_MAX_CONVEXES, width * height <= CS_STATIC_MAX_PIXELS
+   (1920x1080 fits), tile pairs <= CS_STATIC_MAX_PAIRS; beyond a limit the call returns
+   CS_ERR_BUDGET with a message and leaves image and t_final untouched.
+   Every GPU that loads the library holds the array until the process exits.  All calls share it
+   and it keeps the last call's contents (each call clears on its stream what must start at zero),
+   so calls that overlap on the GPU race: issue them on one stream, one after the other.  The first
+   call on a device looks up the array's device address with that device current: make that first
+   call before any stream capture.  The call synchronises its stream once (to read the number of
+   tile pairs) and keeps no state for a backward. */
+#define CS_STATIC_SCRATCH_BYTES (32u << 20)
+#define CS_STATIC_MAX_CONVEXES 65536
+#define CS_STATIC_MAX_PIXELS (1 << 21)
+#define CS_STATIC_MAX_PAIRS (1 << 19)
+cs_status cs_forward_static(const cs_scene *scene, const cs_camera *cam, const cs_settings *settings, float *image,
+                            float *t_final, void *stream);
+
 /* ---- instrumentation (no counterpart in the paper) ------------------------------------------ */
 typedef enum {
     CS_STAGE_PREPROCESS = 0,      /* per-convex projection, hull, lines, tile range, colour */

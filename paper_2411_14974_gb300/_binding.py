@@ -44,6 +44,8 @@ _PROTOTYPES = {
     "cs_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "cs_kernel_launch_count": (ctypes.c_uint64, []),
     "cs_work_counts": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "cs_forward_static": (ctypes.c_int, [ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera),
+                                         ctypes.POINTER(CsSettings), _P, _P, _P]),
 }
 
 STAGES = ("preprocess", "depth_sort", "scan_emit", "tile_sort", "blend", "blend_backward", "preprocess_backward")
