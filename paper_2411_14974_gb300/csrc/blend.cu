@@ -15,9 +15,10 @@
 // The backward walks each tile's list in reverse from the last contributor of each pixel,
 // recovering T before a pair as T_after / (1 - alpha), and accumulates d(loss)/d(record) per
 // convex: the 29 per-pixel terms are summed across the warp by a reduce-scatter (31 shuffles,
-// lane l ends with word l) and added to the convex's gradient record by one coalesced atomic
-// instruction per warp.  A staged record also carries an 8-bit mask of the warps whose 8x4 pixel
-// block can pass the line pre-test at all; the other warps skip it without evaluating.
+// lane l ends with word l), across the warps of the tile in shared memory, and added to the
+// convex's gradient record by one coalesced atomic instruction per (tile, record).  A staged record
+// also carries an 8-bit mask of the warps whose 8x4 pixel block can pass the line pre-test at all;
+// each warp iterates only the records of its ballot-built bit set.
 #include "cs_common.cuh"
 
 namespace cs {
@@ -28,8 +29,8 @@ constexpr int BATCH = 128;  // records staged per round
 constexpr int SREC = 10;    // float4 per staged record
 // staged record: [0] = (sigma', prefilter bound, o, T)   [1] = (r, g, b, -)
 //                [2 + t] = (A_t, B_t, C_t relative to the tile origin, aux)
-//                aux of line 0/1/2 = tile origin minus anchor (x, y), record index (backward);
-//                [1].w = bit w set when warp w may see alpha >= tau (warp-level cull)
+//                aux of line 0/1/2 = tile origin minus anchor (x, y), record index (backward)
+// staged mask: bit w set when warp w may see alpha >= tau (warp-level cull)
 constexpr float LN2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float ex2(float x) {
@@ -48,8 +49,8 @@ __device__ __forceinline__ float rcp(float x) {
     return y;
 }
 
-__device__ __forceinline__ void stage_record(float4 *dst, const float4 *__restrict__ records, uint32_t r,
-                                             float tile_x0, float tile_y0, const Settings &st) {
+__device__ __forceinline__ void stage_record(float4 *dst, uint32_t *mask_out, const float4 *__restrict__ records,
+                                             uint32_t r, float tile_x0, float tile_y0, const Settings &st) {
     const float4 *src = records + (size_t)r * (REC_WORDS / 4);
     const float4 h0 = __ldg(src), h1 = __ldg(src + 1);
     const uint32_t hull = __float_as_uint(h1.w);
@@ -96,7 +97,19 @@ __device__ __forceinline__ void stage_record(float4 *dst, const float4 *__restri
         }
     }
     dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
-    dst[1] = make_float4(h1.x, h1.y, h1.z, __uint_as_float(wmask));
+    dst[1] = make_float4(h1.x, h1.y, h1.z, 0.f);
+    *mask_out = wmask;
+}
+
+// Records of the current batch that warp `wbit` has to evaluate, as a bit set over the batch
+// (uniform across the warp): one ballot per 32 staged records.
+__device__ __forceinline__ void warp_records(const uint32_t *smask, uint32_t nb, uint32_t wbit, int lane,
+                                             uint32_t (&act)[BATCH / 32]) {
+#pragma unroll
+    for (int q = 0; q < BATCH / 32; ++q) {
+        const uint32_t j = (uint32_t)(q * 32 + lane);
+        act[q] = __ballot_sync(0xffffffffu, j < nb && (smask[j] & wbit));
+    }
 }
 
 // Terms of one (pixel, convex) pair kept for the backward.
@@ -166,6 +179,7 @@ __device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
 template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[BATCH * SREC];
+    __shared__ uint32_t smask[BATCH];
     const uint32_t g = blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
     const uint32_t local = g - vd.tile_base;
@@ -177,6 +191,8 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
     const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
     const uint2 range = a.ranges[g];
     const Settings st = a.st;
+    const int lane = threadIdx.x & 31;
+    const uint32_t wbit = 1u << (threadIdx.x >> 5);
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
@@ -186,23 +202,28 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
         if (__syncthreads_and(done)) break;
         const uint32_t nb = min((uint32_t)BATCH, range.y - base);
         if (threadIdx.x < nb)
-            stage_record(srec + threadIdx.x * SREC, a.records, a.pair_vals[base + threadIdx.x],
+            stage_record(srec + threadIdx.x * SREC, smask + threadIdx.x, a.records, a.pair_vals[base + threadIdx.x],
                          (float)(tx * TILE), (float)(ty * TILE), st);
         __syncthreads();
-        if (!done) {
-            const uint32_t wbit = 1u << (threadIdx.x >> 5);
-            for (uint32_t j = 0; j < nb; ++j) {
+        uint32_t act[BATCH / 32];
+        warp_records(smask, nb, wbit, lane, act);
+        if (done) continue;
+#pragma unroll
+        for (int q = 0; q < BATCH / 32; ++q) {
+            uint32_t bits = act[q];
+            while (bits) {
+                const uint32_t j = (uint32_t)(q * 32 + __ffs(bits) - 1);
+                bits &= bits - 1;
                 PairTerms p;
                 const float4 *rec = srec + j * SREC;
-                if (!(__float_as_uint(rec[1].w) & wbit)) continue;  // warp-uniform
                 const int code = eval_pair(rec, lx, ly, st, p);
                 if (COUNT) {
-                    const unsigned T = (unsigned)__float_as_int(rec[0].w);
+                    const unsigned Tl = (unsigned)__float_as_int(rec[0].w);
                     cnt[0]++;
-                    cnt[1] += T;
+                    cnt[1] += Tl;
                     if (code) {
                         cnt[2]++;
-                        cnt[3] += T;
+                        cnt[3] += Tl;
                     }
                     if (code == 2) cnt[4]++;
                 }
@@ -219,6 +240,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
                     break;
                 }
             }
+            if (done) break;
         }
     }
     if (inside) {
@@ -237,6 +259,8 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
                                                                   int64_t image_stride, float4 *__restrict__ grads,
                                                                   unsigned long long *counts) {
     __shared__ float4 srec[BATCH * SREC];
+    __shared__ uint32_t smask[BATCH];
+    __shared__ float sgrad[BATCH * 32];  // per staged record: the gradient-record words of this tile
     __shared__ uint32_t s_max_last[BLEND_THREADS / 32];
     const uint32_t g = blockIdx.x;
     const int v = find_view(a.views, a.n_views, g);
@@ -280,13 +304,21 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
         const uint32_t nb = end - start;
         __syncthreads();
         if (threadIdx.x < nb)
-            stage_record(srec + threadIdx.x * SREC, a.records, a.pair_vals[start + threadIdx.x],
+            stage_record(srec + threadIdx.x * SREC, smask + threadIdx.x, a.records, a.pair_vals[start + threadIdx.x],
                          (float)(tx * TILE), (float)(ty * TILE), st);
+        for (uint32_t i = threadIdx.x; i < nb * 32; i += BLEND_THREADS) sgrad[i] = 0.f;
         __syncthreads();
         const uint32_t wbit = 1u << (threadIdx.x >> 5);
-        for (int j = (int)nb - 1; j >= 0; --j) {
+        uint32_t act[BATCH / 32];
+        warp_records(smask, nb, wbit, lane, act);
+#pragma unroll
+        for (int q = BATCH / 32 - 1; q >= 0; --q) {
+          uint32_t bits = act[q];
+          while (bits) {  // warp-uniform, from the back of the batch
+            const int jj = 31 - __clz(bits);
+            bits &= ~(1u << jj);
+            const int j = q * 32 + jj;
             const float4 *rec = srec + j * SREC;
-            if (!(__float_as_uint(rec[1].w) & wbit)) continue;  // warp-uniform
             const uint32_t idx = start + (uint32_t)j;
             PairTerms p;
             const int code = idx < last ? eval_pair(rec, lx, ly, st, p) : -1;
@@ -359,8 +391,17 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
             const int slot = lane < 24 ? lane % 3 : 3;
             if (slot == 0) word = fmaf(rec[2].w, g2, word);
             else if (slot == 1) word = fmaf(rec[3].w, g1, word);
-            const uint32_t r = __float_as_uint(rec[4].w);
-            if (lane < 29 && word != 0.f) atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
+            if (lane < 29 && word != 0.f) atomicAdd(sgrad + j * 32 + lane, word);
+          }
+        }
+        __syncthreads();
+        // one coalesced global atomic per (tile, record, word) for what the warps accumulated
+        for (uint32_t i = threadIdx.x; i < nb * 32; i += BLEND_THREADS) {
+            const float w = sgrad[i];
+            if (w != 0.f) {
+                const uint32_t r = __float_as_uint(srec[(i >> 5) * SREC + 4].w);
+                atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + (i & 31), w);
+            }
         }
         end = start;
     }
