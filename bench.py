@@ -121,6 +121,68 @@ def oracle_sample(sc, cam, npix, seed=0):
     return time.perf_counter() - t0, oracle.num_threads()
 
 
+def serving_bench(dev_index, n_requests=96, seed=0):
+    """Serving loop: three resident scenes (300k, 1M, 3M convexes), view requests of mixed
+    resolution (800x800, 1280x720, 1920x1080) and random poses on spheres of radius 3-5.
+    The batched server (up to 32 views per launch, 32 GB transient budget) and one-view-at-a-time
+    serving (max_batch 1) see the same requests: first all at once (capacity), then as a Poisson
+    trace at 80% of the one-at-a-time capacity (latency at equal load)."""
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    from paper_2411_14974_gb300 import synthetic as syn
+    dev = torch.device("cuda", dev_index)
+    sizes_n = [300_000, 1_000_000, 3_000_000]
+    scenes = [cs.SceneTensors.from_numpy(syn.surface_scene(20 + i, n), dev) for i, n in enumerate(sizes_n)]
+    rng = np.random.default_rng(seed)
+    res = [(800, 800), (1280, 720), (1920, 1080)]
+    reqs = []
+    for _ in range(n_requests):
+        w, h = res[rng.integers(3)]
+        cam = syn.sphere_cameras(1, w, h, (3.0, 5.0), seed=int(rng.integers(1 << 30)))[0]
+        reqs.append((int(rng.integers(3)), cam))
+    outs = [torch.empty((3, c.height, c.width), device=dev) for _, c in reqs]
+
+    def run(max_batch, arrivals=None):
+        with cs.Server(dev_index, budget_bytes=32 << 30, max_batch=max_batch) as srv:
+            sids = [srv.add_scene(s) for s in scenes]
+            for i in range(3):  # warm the pool and the kernels
+                srv.submit(sids[i], reqs[0][1], outs[0])
+            got = 0
+            while got < 3:
+                got += len(srv.poll(16, 100))
+            done = []
+            t0 = time.perf_counter()
+            for i, (si, cam) in enumerate(reqs):
+                if arrivals is not None:
+                    wait = t0 + arrivals[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                srv.submit(sids[si], cam, outs[i])
+                done += srv.poll(256, 0)
+            while len(done) < len(reqs):
+                done += srv.poll(256, 50)
+            t1 = time.perf_counter()
+            st = srv.stats()
+        lat = sorted(d["latency_ms"] for d in done)
+        n = len(lat)
+        return dict(p50_ms=lat[n // 2], p99_ms=lat[min(n - 1, int(round(0.99 * (n - 1))))],
+                    views_s=n / (t1 - t0), mean_batch=float(np.mean([d["batch_size"] for d in done])),
+                    largest_batch=int(st["largest_batch"]), peak_gb=st["peak_bytes"] / 1e9,
+                    ok=all(d["status"] == "ok" for d in done))
+
+    cap1 = run(1)
+    capb = run(32)
+    lam = 0.8 * cap1["views_s"]
+    arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / lam, n_requests))
+    load1 = run(1, arrivals)
+    loadb = run(32, arrivals)
+    return dict(requests=n_requests, scenes=sizes_n, resolutions=["800x800", "1280x720", "1920x1080"],
+                arrival_rate_views_s=lam, p50_ms=loadb["p50_ms"], p99_ms=loadb["p99_ms"],
+                views_s=capb["views_s"], batched_at_load=loadb, one_at_a_time_at_load=load1,
+                batched_capacity=capb, one_at_a_time_capacity=cap1)
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -290,6 +352,8 @@ def run_ours(args):
         d2h = host_img.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
         out["e2e"] = dict(value=pixels_per_step / e2e_s / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
                           d2h_bytes_per_step=int(d2h), ms_per_step=e2e_s * 1e3)
+        # serving loop (continuous batching) against one-view-at-a-time on the same requests
+        out["serving"] = serving_bench(local)
         # CPU oracle on a bounded sample of the same workload
         if ws == 1:
             import oracle

@@ -189,6 +189,52 @@ cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_cam
 cs_status cs_forward_static(const cs_scene *scene, const cs_camera *cam, const cs_settings *settings, float *image,
                             float *t_final, void *stream);
 
+/* ---- serving: continuous batching of novel-view requests (no counterpart in the paper) -------
+   A server keeps several scenes resident (device buffers owned by the caller, registered with
+   cs_server_add_scene) and renders view requests of mixed resolution.  A worker thread admits
+   queued requests in arrival order into a batch of at most max_batch views, as long as the
+   estimated transient memory of the batch plus the batches still on the GPU fits the memory
+   budget; requests that arrive while earlier batches are on the GPU join the next batch as soon
+   as memory frees up.  A batch is binned and sorted as one (the view index lives in the tile
+   key) and blended by one kernel launch over the (view, tile) pairs of all its views; batches
+   alternate between two streams, so the preprocess and sorts of one overlap the blend of the
+   previous one.  Each view's image is identical to rendering it alone with cs_forward.
+   Images are written to caller-owned device buffers [3][H][W] that must stay alive until the
+   request's completion has been polled.  All calls are thread-safe. */
+typedef struct cs_server cs_server;
+
+typedef struct {
+    uint64_t id;          /* request id returned by cs_server_submit */
+    int32_t status;       /* CS_OK, CS_ERR_BUDGET (larger than the whole budget), CS_ERR_STATE
+                             (scene removed while queued), CS_ERR_CUDA */
+    int32_t batch_size;   /* views in the batch that rendered it */
+    double queue_ms;      /* submit -> batch admitted */
+    double latency_ms;    /* submit -> image complete on the device */
+} cs_completion;
+
+/* memory_budget_bytes bounds the estimated transient device memory of admitted batches;
+   1 <= max_batch <= 1024.  settings apply to every request. */
+cs_status cs_server_create(int32_t device, size_t memory_budget_bytes, int32_t max_batch, const cs_settings *settings,
+                           cs_server **out);
+/* Stops the worker after the queued requests complete, then frees the server. */
+void cs_server_destroy(cs_server *srv);
+/* Registers a resident scene (device pointers as for cs_forward; the caller keeps them alive and
+   unchanged while the scene is registered).  Returns its id in *scene_id. */
+cs_status cs_server_add_scene(cs_server *srv, const cs_scene *scene, int32_t *scene_id);
+/* Unregisters a scene; its queued requests complete with CS_ERR_STATE, batches already admitted
+   finish normally.  Returns once no admitted batch still reads the scene. */
+cs_status cs_server_remove_scene(cs_server *srv, int32_t scene_id);
+/* Queues a view of scene_id; image: device [3][cam->height][cam->width].  CS_ERR_ARG for a bad
+   camera or unknown scene (nothing is queued). */
+cs_status cs_server_submit(cs_server *srv, int32_t scene_id, const cs_camera *cam, float *image,
+                           uint64_t *request_id);
+/* Moves up to max completions into out (oldest first); waits up to wait_ms milliseconds for the
+   first one when none is ready (0 = do not wait). */
+cs_status cs_server_poll(cs_server *srv, cs_completion *out, int32_t max, int32_t *n_out, int32_t wait_ms);
+/* Counters: [0] requests completed, [1] batches run, [2] largest batch, [3] peak estimated bytes
+   in flight, [4] requests queued now, [5] requests on the GPU now. */
+cs_status cs_server_stats(cs_server *srv, uint64_t *stats);
+
 /* ---- instrumentation (no counterpart in the paper) ------------------------------------------ */
 typedef enum {
     CS_STAGE_PREPROCESS = 0,      /* per-convex projection, hull, lines, tile range, colour */

@@ -24,6 +24,11 @@ class CsScene(ctypes.Structure):
                 ("k", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
 
 
+class CsCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
 # every entry point declared in include/convex_splat.h, with (restype, argtypes)
 _P = ctypes.c_void_p
 _PROTOTYPES = {
@@ -46,6 +51,16 @@ _PROTOTYPES = {
     "cs_work_counts": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "cs_forward_static": (ctypes.c_int, [ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera),
                                          ctypes.POINTER(CsSettings), _P, _P, _P]),
+    "cs_server_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32,
+                                        ctypes.POINTER(CsSettings), ctypes.POINTER(_P)]),
+    "cs_server_destroy": (None, [_P]),
+    "cs_server_add_scene": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(ctypes.c_int32)]),
+    "cs_server_remove_scene": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "cs_server_submit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(CsCamera), _P,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "cs_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(CsCompletion), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+    "cs_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
 STAGES = ("preprocess", "depth_sort", "scan_emit", "tile_sort", "blend", "blend_backward", "preprocess_backward")

@@ -289,3 +289,79 @@ def step_host(scene_host: dict, sh_degree: int, cams: Sequence, settings: Option
                                 ptr(g.get("sigma")), ptr(g.get("opacity")), ptr(g.get("sh")),
                                 _stream_ptr(torch.device("cuda", device)))
     B.check(code, "cs_step_host")
+
+
+# ---- serving -----------------------------------------------------------------------------------
+class Server:
+    """Continuous-batching view server over resident scenes (cs_server_* in the C ABI).
+
+    Requests are queued with submit(); a worker thread in the library admits them into batches
+    by an estimated memory budget and renders each batch with one binning/sort and one blend
+    launch; poll() returns completions with their latencies."""
+
+    STATUS = {0: "ok", 1: "arg", 2: "cuda", 3: "nomem", 4: "budget", 5: "timeout", 6: "device", 7: "state"}
+
+    def __init__(self, device: int = 0, budget_bytes: int = 32 << 30, max_batch: int = 32,
+                 settings: Optional[Settings] = None):
+        h = ctypes.c_void_p()
+        s = (settings or Settings()).struct()
+        B.check(B.lib().cs_server_create(int(device), int(budget_bytes), int(max_batch), ctypes.byref(s),
+                                         ctypes.byref(h)), "cs_server_create")
+        self.handle = h
+        self.device = device
+        self._scenes = {}
+        self._outputs = {}
+
+    def add_scene(self, scene: SceneTensors) -> int:
+        sid = ctypes.c_int32()
+        sc = scene.struct()
+        B.check(B.lib().cs_server_add_scene(self.handle, ctypes.byref(sc), ctypes.byref(sid)), "cs_server_add_scene")
+        self._scenes[sid.value] = scene
+        return sid.value
+
+    def remove_scene(self, sid: int):
+        B.check(B.lib().cs_server_remove_scene(self.handle, int(sid)), "cs_server_remove_scene")
+        self._scenes.pop(sid, None)
+
+    def submit(self, sid: int, cam, image: torch.Tensor) -> int:
+        """Queue a view; image: contiguous float32 CUDA tensor [3][H][W], kept alive until polled."""
+        rid = ctypes.c_uint64()
+        c = camera_struct(cam)
+        B.check(B.lib().cs_server_submit(self.handle, int(sid), ctypes.byref(c), image.data_ptr(), ctypes.byref(rid)),
+                "cs_server_submit")
+        self._outputs[rid.value] = image
+        return rid.value
+
+    def poll(self, max_n: int = 256, wait_ms: int = 0) -> list:
+        buf = (B.CsCompletion * max_n)()
+        n = ctypes.c_int32()
+        B.check(B.lib().cs_server_poll(self.handle, buf, max_n, ctypes.byref(n), int(wait_ms)), "cs_server_poll")
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            self._outputs.pop(c.id, None)
+            out.append(dict(id=c.id, status=self.STATUS.get(c.status, str(c.status)), batch_size=c.batch_size,
+                            queue_ms=c.queue_ms, latency_ms=c.latency_ms))
+        return out
+
+    def stats(self) -> dict:
+        a = (ctypes.c_uint64 * 6)()
+        B.check(B.lib().cs_server_stats(self.handle, a), "cs_server_stats")
+        return dict(completed=a[0], batches=a[1], largest_batch=a[2], peak_bytes=a[3], queued=a[4], on_gpu=a[5])
+
+    def close(self):
+        if self.handle:
+            B.lib().cs_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
