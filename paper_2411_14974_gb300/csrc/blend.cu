@@ -1,9 +1,11 @@
 // Per-tile blending of the convex tile rasterizer, forward and backward.
 //
 // One CTA of 256 threads per 16x16 tile; each warp owns an 8x4 pixel block, each thread one
-// pixel.  The tile's depth-ordered convex records are staged in shared memory in batches (one
-// record per thread, 128-byte coalesced gather), re-expressed relative to the tile origin so
-// that every line is two FMAs per pixel.  Per pixel and convex (Eq. S1, S2 and 5):
+// pixel, and the warps work independently (no CTA barrier).  A warp walks the tile's
+// depth-ordered records 32 at a time: each lane stages one record in the warp's shared-memory
+// slice (128-byte gather), re-expressed relative to the warp's block origin so that every line
+// is two FMAs per pixel, and tests whether any pixel of the block can pass the line pre-test;
+// the warp then evaluates only the records of the resulting ballot.  Per pixel and convex (Eq. S1, S2 and 5):
 //     s_t  = log2(e) d delta L_t(q)                     (T lines, 2 FMA each)
 //     phi2 = max_t s_t + log2 sum_t 2^(s_t - max)       (= log2(e) phi)
 //     I    = 1 / (1 + 2^(d sigma phi2))                 (= Sigmoid(-d sigma phi))
@@ -15,22 +17,20 @@
 // The backward walks each tile's list in reverse from the last contributor of each pixel,
 // recovering T before a pair as T_after / (1 - alpha), and accumulates d(loss)/d(record) per
 // convex: the 29 per-pixel terms are summed across the warp by a reduce-scatter (31 shuffles,
-// lane l ends with word l), across the warps of the tile in shared memory, and added to the
-// convex's gradient record by one coalesced atomic instruction per (tile, record).  A staged record
-// also carries an 8-bit mask of the warps whose 8x4 pixel block can pass the line pre-test at all;
-// each warp iterates only the records of its ballot-built bit set.
+// lane l ends with word l) and added to the convex's gradient record by one coalesced atomic
+// instruction per (warp, record).
 #include "cs_common.cuh"
 
 namespace cs {
 namespace {
 
 constexpr int BLEND_THREADS = 256;
-constexpr int BATCH = 128;  // records staged per round
-constexpr int SREC = 10;    // float4 per staged record
-// staged record: [0] = (sigma', prefilter bound, o, T)   [1] = (r, g, b, -)
-//                [2 + t] = (A_t, B_t, C_t relative to the tile origin, aux)
-//                aux of line 0/1/2 = tile origin minus anchor (x, y), record index (backward)
-// staged mask: bit w set when warp w may see alpha >= tau (warp-level cull)
+constexpr int WARPS = BLEND_THREADS / 32;
+constexpr int SREC = 10;  // float4 per staged record
+// staged record (one per lane of a warp, for that warp's 8x4 pixel block):
+//   [0] = (sigma', pre-test bound, o, T)   [1] = (r, g, b, record index)
+//   [2 + t] = (A_t, B_t, C_t relative to the block origin, aux); aux of lines 0 and 1 = block
+//   origin minus the record's anchor vertex (x, y), used by the backward
 constexpr float LN2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float ex2(float x) {
@@ -49,12 +49,15 @@ __device__ __forceinline__ float rcp(float x) {
     return y;
 }
 
-__device__ __forceinline__ void stage_record(float4 *dst, uint32_t *mask_out, const float4 *__restrict__ records,
-                                             uint32_t r, float tile_x0, float tile_y0, const Settings &st) {
+// Stage record r for the 8x4 pixel block whose first pixel centre is (ox + 0.5, oy + 0.5) in
+// image coordinates; lines are re-based to (ox, oy).  Returns false when no pixel of the block
+// can pass the line pre-test: for some line, its smallest value over the block's pixel centres
+// exceeds the bound (with a margin for the per-pixel rounding).
+__device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
+                                             float oy, const Settings &st) {
     const float4 *src = records + (size_t)r * (REC_WORDS / 4);
     const float4 h0 = __ldg(src), h1 = __ldg(src + 1);
-    const uint32_t hull = __float_as_uint(h1.w);
-    const int T = (int)hull_pack_count(hull);
+    const int T = (int)hull_pack_count(__float_as_uint(h1.w));
     float L[3 * KMAX];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
@@ -65,51 +68,32 @@ __device__ __forceinline__ void stage_record(float4 *dst, uint32_t *mask_out, co
             L[4 * q] = L[4 * q + 1] = L[4 * q + 2] = L[4 * q + 3] = 0.f;
         }
     }
-    const float offx = tile_x0 - h0.x, offy = tile_y0 - h0.y;
-    // prefilter: alpha < tau whenever sigma' * max_t s_t > log2(o/tau - 1) (phi2 >= max_t s_t);
-    // widened slightly so that it never rejects a pair the full evaluation keeps
+    const float offx = ox - h0.x, offy = oy - h0.y;
+    // pre-test: alpha < tau whenever sigma' max_t s_t > log2(o/tau - 1) (phi2 >= max_t s_t); the
+    // bound is widened so that it never rejects a pair the full evaluation keeps
     float bound = __int_as_float(0x7f800000);
     if (st.tau > 0.f) {
         const float x = h0.w / st.tau - 1.0f;
         if (isfinite(x)) {
-            const float b = log2f(x) / h0.z;
+            const float b = lg2(x) * rcp(h0.z);
             bound = b + fabsf(b) * 0x1p-10f + 0x1p-10f;
         }
     }
-    // warp cull: warp w covers pixel centres lx in [8(w&1) + .5, 8(w&1) + 7.5], ly in
-    // [4(w>>1) + .5, 4(w>>1) + 3.5]; if for some line the smallest value over that block exceeds
-    // the bound (with a margin covering the per-pixel rounding), no pixel of the warp passes
-    uint32_t wmask = 0xffu;
+    bool pass = true;
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
         if (t < T) {
             const float A = L[3 * t], B = L[3 * t + 1], C = L[3 * t + 2];
             const float Cp = fmaf(A, offx, fmaf(B, offy, C));
-            const float aux = t == 0 ? offx : (t == 1 ? offy : __uint_as_float(r));
-            dst[2 + t] = make_float4(A, B, Cp, aux);
-            const float margin = (fabsf(Cp) + 16.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
-#pragma unroll
-            for (int w = 0; w < BLEND_THREADS / 32; ++w) {
-                const float x0 = (float)((w & 1) * 8) + 0.5f, y0 = (float)((w >> 1) * 4) + 0.5f;
-                const float mx = fminf(A * x0, A * (x0 + 7.f)), my = fminf(B * y0, B * (y0 + 3.f));
-                if (Cp + mx + my > bound + margin) wmask &= ~(1u << w);
-            }
+            dst[2 + t] = make_float4(A, B, Cp, t == 0 ? offx : offy);
+            const float margin = (fabsf(Cp) + 8.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
+            const float mn = Cp + fminf(0.5f * A, 7.5f * A) + fminf(0.5f * B, 3.5f * B);
+            pass = pass && !(mn > bound + margin);
         }
     }
     dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
-    dst[1] = make_float4(h1.x, h1.y, h1.z, 0.f);
-    *mask_out = wmask;
-}
-
-// Records of the current batch that warp `wbit` has to evaluate, as a bit set over the batch
-// (uniform across the warp): one ballot per 32 staged records.
-__device__ __forceinline__ void warp_records(const uint32_t *smask, uint32_t nb, uint32_t wbit, int lane,
-                                             uint32_t (&act)[BATCH / 32]) {
-#pragma unroll
-    for (int q = 0; q < BATCH / 32; ++q) {
-        const uint32_t j = (uint32_t)(q * 32 + lane);
-        act[q] = __ballot_sync(0xffffffffu, j < nb && (smask[j] & wbit));
-    }
+    dst[1] = make_float4(h1.x, h1.y, h1.z, __uint_as_float(r));
+    return pass;
 }
 
 // Terms of one (pixel, convex) pair kept for the backward.
@@ -164,69 +148,77 @@ __device__ __forceinline__ void flush_counts(unsigned long long *dst, const unsi
     }
 }
 
+__device__ __forceinline__ void count_pair(unsigned long long (&cnt)[NCOUNT], const float4 *rec, int code) {
+    const unsigned T = (unsigned)__float_as_int(rec[0].w);
+    cnt[0]++;
+    cnt[1] += T;
+    if (code) {
+        cnt[2]++;
+        cnt[3] += T;
+    }
+    if (code == 2) cnt[4]++;
+}
+
 __device__ __forceinline__ int find_view(const ViewDesc *__restrict__ views, int n_views, uint32_t g) {
     int v = 0;
     while (v + 1 < n_views && g >= views[v + 1].tile_base) ++v;
     return v;
 }
 
-__device__ __forceinline__ void pixel_of(int tid, int &lx, int &ly) {
-    const int w = tid >> 5, lane = tid & 31;
-    lx = (w & 1) * 8 + (lane & 7);
-    ly = (w >> 1) * 4 + (lane >> 3);
+// tile coordinates, this thread's pixel and its warp's block origin (image coordinates)
+struct BlockPos {
+    int px, py;        // pixel
+    float ox, oy;      // origin of the warp's 8x4 block
+    float lx, ly;      // pixel centre relative to the block origin
+    bool inside;
+};
+
+__device__ __forceinline__ BlockPos block_pos(const ViewDesc &vd, uint32_t g) {
+    const uint32_t local = g - vd.tile_base;
+    const int tx = (int)(local % (uint32_t)vd.tiles_x), ty = (int)(local / (uint32_t)vd.tiles_x);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
+    BlockPos b;
+    b.px = bx + (lane & 7);
+    b.py = by + (lane >> 3);
+    b.ox = (float)bx;
+    b.oy = (float)by;
+    b.lx = (float)(lane & 7) + 0.5f;
+    b.ly = (float)(lane >> 3) + 0.5f;
+    b.inside = b.px < vd.width && b.py < vd.height;
+    return b;
 }
 
 template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
-    __shared__ float4 srec[BATCH * SREC];
-    __shared__ uint32_t smask[BATCH];
+    __shared__ float4 srec[WARPS][32 * SREC];
     const uint32_t g = blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
-    const uint32_t local = g - vd.tile_base;
-    const int tx = (int)(local % (uint32_t)vd.tiles_x), ty = (int)(local / (uint32_t)vd.tiles_x);
-    int lxi, lyi;
-    pixel_of(threadIdx.x, lxi, lyi);
-    const int px = tx * TILE + lxi, py = ty * TILE + lyi;
-    const bool inside = px < vd.width && py < vd.height;
-    const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
+    const BlockPos bp = block_pos(vd, g);
     const uint2 range = a.ranges[g];
     const Settings st = a.st;
     const int lane = threadIdx.x & 31;
-    const uint32_t wbit = 1u << (threadIdx.x >> 5);
+    float4 *wrec = srec[threadIdx.x >> 5];
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
-    bool done = !inside;
-    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
-    for (uint32_t base = range.x; base < range.y; base += BATCH) {
-        if (__syncthreads_and(done)) break;
-        const uint32_t nb = min((uint32_t)BATCH, range.y - base);
-        if (threadIdx.x < nb)
-            stage_record(srec + threadIdx.x * SREC, smask + threadIdx.x, a.records, a.pair_vals[base + threadIdx.x],
-                         (float)(tx * TILE), (float)(ty * TILE), st);
-        __syncthreads();
-        uint32_t act[BATCH / 32];
-        warp_records(smask, nb, wbit, lane, act);
-        if (done) continue;
-#pragma unroll
-        for (int q = 0; q < BATCH / 32; ++q) {
-            uint32_t bits = act[q];
+    bool done = !bp.inside;
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
+    for (uint32_t base = range.x; base < range.y; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const uint32_t n = min(32u, range.y - base);
+        bool pass = false;
+        if ((uint32_t)lane < n) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[base + lane], bp.ox, bp.oy, st);
+        __syncwarp();
+        uint32_t bits = __ballot_sync(0xffffffffu, pass);
+        if (!done) {
             while (bits) {
-                const uint32_t j = (uint32_t)(q * 32 + __ffs(bits) - 1);
+                const uint32_t j = (uint32_t)(__ffs(bits) - 1);
                 bits &= bits - 1;
+                const float4 *rec = wrec + j * SREC;
                 PairTerms p;
-                const float4 *rec = srec + j * SREC;
-                const int code = eval_pair(rec, lx, ly, st, p);
-                if (COUNT) {
-                    const unsigned Tl = (unsigned)__float_as_int(rec[0].w);
-                    cnt[0]++;
-                    cnt[1] += Tl;
-                    if (code) {
-                        cnt[2]++;
-                        cnt[3] += Tl;
-                    }
-                    if (code == 2) cnt[4]++;
-                }
+                const int code = eval_pair(rec, bp.lx, bp.ly, st, p);
+                if (COUNT) count_pair(cnt, rec, code);
                 if (code != 2) continue;
                 const float4 c = rec[1];
                 const float wgt = p.alpha * T;
@@ -240,11 +232,11 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
                     break;
                 }
             }
-            if (done) break;
         }
+        __syncwarp();
     }
-    if (inside) {
-        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)py * vd.width + px;
+    if (bp.inside) {
+        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)bp.py * vd.width + bp.px;
         vd.image[pix] = fmaf(T, st.bg[0], C0);
         vd.image[hw + pix] = fmaf(T, st.bg[1], C1);
         vd.image[2 * hw + pix] = fmaf(T, st.bg[2], C2);
@@ -258,28 +250,20 @@ template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                   int64_t image_stride, float4 *__restrict__ grads,
                                                                   unsigned long long *counts) {
-    __shared__ float4 srec[BATCH * SREC];
-    __shared__ uint32_t smask[BATCH];
-    __shared__ float sgrad[BATCH * 32];  // per staged record: the gradient-record words of this tile
-    __shared__ uint32_t s_max_last[BLEND_THREADS / 32];
+    __shared__ float4 srec[WARPS][32 * SREC];
     const uint32_t g = blockIdx.x;
     const int v = find_view(a.views, a.n_views, g);
     const ViewDesc &vd = a.views[v];
-    const uint32_t local = g - vd.tile_base;
-    const int tx = (int)(local % (uint32_t)vd.tiles_x), ty = (int)(local / (uint32_t)vd.tiles_x);
-    int lxi, lyi;
-    pixel_of(threadIdx.x, lxi, lyi);
-    const int px = tx * TILE + lxi, py = ty * TILE + lyi;
-    const bool inside = px < vd.width && py < vd.height;
-    const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
+    const BlockPos bp = block_pos(vd, g);
     const uint2 range = a.ranges[g];
     const Settings st = a.st;
     const int lane = threadIdx.x & 31;
+    float4 *wrec = srec[threadIdx.x >> 5];
 
     float Tc = 1.0f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
     uint32_t last = 0;
-    if (inside) {
-        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)py * vd.width + px;
+    if (bp.inside) {
+        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)bp.py * vd.width + bp.px;
         const float *dl = dL_dimage + v * image_stride;
         G0 = dl[pix];
         G1 = dl[hw + pix];
@@ -289,120 +273,90 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
     }
     // colour seen behind the current pair, T_after * (its colour) summed from the back
     float S0 = Tc * st.bg[0], S1 = Tc * st.bg[1], S2 = Tc * st.bg[2];
-    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
-    uint32_t wl = last;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
-    if (lane == 0) s_max_last[threadIdx.x >> 5] = wl;
-    __syncthreads();
-    uint32_t end = range.x;
-#pragma unroll
-    for (int q = 0; q < BLEND_THREADS / 32; ++q) end = max(end, s_max_last[q]);
-
-    while (end > range.x) {
-        const uint32_t start = end > range.x + BATCH ? end - BATCH : range.x;
-        const uint32_t nb = end - start;
-        __syncthreads();
-        if (threadIdx.x < nb)
-            stage_record(srec + threadIdx.x * SREC, smask + threadIdx.x, a.records, a.pair_vals[start + threadIdx.x],
-                         (float)(tx * TILE), (float)(ty * TILE), st);
-        for (uint32_t i = threadIdx.x; i < nb * 32; i += BLEND_THREADS) sgrad[i] = 0.f;
-        __syncthreads();
-        const uint32_t wbit = 1u << (threadIdx.x >> 5);
-        uint32_t act[BATCH / 32];
-        warp_records(smask, nb, wbit, lane, act);
-#pragma unroll
-        for (int q = BATCH / 32 - 1; q >= 0; --q) {
-          uint32_t bits = act[q];
-          while (bits) {  // warp-uniform, from the back of the batch
-            const int jj = 31 - __clz(bits);
-            bits &= ~(1u << jj);
-            const int j = q * 32 + jj;
-            const float4 *rec = srec + j * SREC;
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
+    const uint32_t wend = __reduce_max_sync(0xffffffffu, last);
+    for (uint32_t end = max(wend, range.x); end > range.x;) {
+        const uint32_t start = end > range.x + 32 ? end - 32 : range.x;
+        const uint32_t n = end - start;
+        bool pass = false;
+        if ((uint32_t)lane < n) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[start + lane], bp.ox, bp.oy, st);
+        __syncwarp();
+        uint32_t bits = __ballot_sync(0xffffffffu, pass);
+        while (bits) {  // warp-uniform, from the back of the chunk
+            const int j = 31 - __clz(bits);
+            bits &= ~(1u << j);
+            const float4 *rec = wrec + j * SREC;
             const uint32_t idx = start + (uint32_t)j;
             PairTerms p;
-            const int code = idx < last ? eval_pair(rec, lx, ly, st, p) : -1;
+            const int code = idx < last ? eval_pair(rec, bp.lx, bp.ly, st, p) : -1;
             const bool on = code == 2;
-            if (COUNT && code >= 0) {
-                const unsigned T = (unsigned)__float_as_int(rec[0].w);
-                cnt[0]++;
-                cnt[1] += T;
-                if (code) {
-                    cnt[2]++;
-                    cnt[3] += T;
-                }
-                if (on) cnt[4]++;
-            }
+            if (COUNT && code >= 0) count_pair(cnt, rec, code);
             if (!__any_sync(0xffffffffu, on)) continue;
             const float4 h0 = rec[0];
             const int T = __float_as_int(h0.w);
             // per-pixel terms in gradient-record word order: 3t+0 = g_t lx, 3t+1 = g_t ly,
             // 3t+2 = g_t, 24 dsigma', 25 dopacity, 26..28 dcolour
-            float v[32];
+            float v32[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            for (int q = 0; q < 32; ++q) v32[q] = 0.f;
             if (on) {
                 const float4 c = rec[1];
                 const float om = 1.0f - p.alpha;
                 const float inv = __frcp_rn(om);
                 const float Tn = Tc * inv;  // transmittance in front of this pair
-                const float dalpha = G0 * (Tn * c.x - S0 * inv) + G1 * (Tn * c.y - S1 * inv) + G2 * (Tn * c.z - S2 * inv);
+                const float dalpha =
+                    G0 * (Tn * c.x - S0 * inv) + G1 * (Tn * c.y - S1 * inv) + G2 * (Tn * c.z - S2 * inv);
                 const float ta = Tn * p.alpha;
-                v[G_RGB] = G0 * ta;
-                v[G_RGB + 1] = G1 * ta;
-                v[G_RGB + 2] = G2 * ta;
+                v32[G_RGB] = G0 * ta;
+                v32[G_RGB + 1] = G1 * ta;
+                v32[G_RGB + 2] = G2 * ta;
                 S0 = fmaf(ta, c.x, S0);
                 S1 = fmaf(ta, c.y, S1);
                 S2 = fmaf(ta, c.z, S2);
                 Tc = Tn;
                 if (p.oI < st.alpha_max) {
-                    v[G_OPA] = dalpha * p.I;
+                    v32[G_OPA] = dalpha * p.I;
                     const float dI = dalpha * h0.z;
                     // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
                     const float dx = -dI * LN2 * p.z * p.I * p.I;
-                    v[G_SIG] = dx * p.phi2;
+                    v32[G_SIG] = dx * p.phi2;
                     const float dphi2 = dx * h0.x * rcp(p.S);
 #pragma unroll
                     for (int t = 0; t < KMAX; ++t) {
                         if (t < T) {
                             const float gt = dphi2 * p.e[t];
-                            v[3 * t] = gt * lx;
-                            v[3 * t + 1] = gt * ly;
-                            v[3 * t + 2] = gt;
+                            v32[3 * t] = gt * bp.lx;
+                            v32[3 * t + 1] = gt * bp.ly;
+                            v32[3 * t + 2] = gt;
                         }
                     }
                 }
             }
-            // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v[l]
+            // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v32[l]
 #pragma unroll
             for (int h = 16; h >= 1; h >>= 1) {
                 const bool upper = (lane & h) != 0;
 #pragma unroll
                 for (int q = 0; q < h; ++q) {
-                    const float send = upper ? v[q] : v[q + h];
-                    const float keep = upper ? v[q + h] : v[q];
-                    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+                    const float send = upper ? v32[q] : v32[q + h];
+                    const float keep = upper ? v32[q + h] : v32[q];
+                    v32[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
                 }
             }
-            float word = v[0];
-            // s = A (lx + offx) + B (ly + offy) + C: dA = sum(g lx) + offx sum(g), dB likewise
+            float word = v32[0];
+            // s = A (lx + ox - ax) + B (ly + oy - ay) + C: dA = sum(g lx) + (ox - ax) sum(g), dB likewise
             const float g2 = __shfl_down_sync(0xffffffffu, word, 2);
             const float g1 = __shfl_down_sync(0xffffffffu, word, 1);
-            const int slot = lane < 24 ? lane % 3 : 3;
-            if (slot == 0) word = fmaf(rec[2].w, g2, word);
-            else if (slot == 1) word = fmaf(rec[3].w, g1, word);
-            if (lane < 29 && word != 0.f) atomicAdd(sgrad + j * 32 + lane, word);
-          }
-        }
-        __syncthreads();
-        // one coalesced global atomic per (tile, record, word) for what the warps accumulated
-        for (uint32_t i = threadIdx.x; i < nb * 32; i += BLEND_THREADS) {
-            const float w = sgrad[i];
-            if (w != 0.f) {
-                const uint32_t r = __float_as_uint(srec[(i >> 5) * SREC + 4].w);
-                atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + (i & 31), w);
+            const uint32_t r = __float_as_uint(rec[1].w);
+            if (lane < 24) {
+                const int slot = lane % 3;
+                if (slot == 0) word = fmaf(rec[2].w, g2, word);
+                else if (slot == 1) word = fmaf(rec[3].w, g1, word);
             }
+            if (lane < 29 && word != 0.f)
+                atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
         }
+        __syncwarp();
         end = start;
     }
     if (COUNT) flush_counts(counts, cnt);
