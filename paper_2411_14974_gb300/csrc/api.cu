@@ -274,6 +274,7 @@ void cs::state_free(cs_fwd_state *s) {
     pool_free(s->depth_keys, st);
     pool_free(s->rects, st);
     pool_free(s->counts, st);
+    pool_free(s->bboxes, st);
     pool_free(s->pair_keys, st);
     pool_free(s->pair_vals, st);
     pool_free(s->ranges, st);
@@ -320,6 +321,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     CS_TRY(pool_alloc(ctx, (void **)&s->depth_keys, (size_t)R * 4, stream), "alloc depth keys");
     CS_TRY(pool_alloc(ctx, (void **)&s->rects, (size_t)R * 8, stream), "alloc rects");
     CS_TRY(pool_alloc(ctx, (void **)&s->counts, (size_t)R * 4, stream), "alloc counts");
+    CS_TRY(pool_alloc(ctx, (void **)&s->bboxes, (size_t)R * 16, stream), "alloc boxes");
     CS_TRY(pool_alloc(ctx, (void **)&s->ranges, (size_t)tiles * 8, stream), "alloc ranges");
     CS_TRY(pool_alloc(ctx, (void **)&s->n_last, pix_total * 4, stream), "alloc n_last");
     {
@@ -341,7 +343,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
            "copy views");
     {
         StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
-        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts};
+        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
     }
     // depth order of the records
@@ -406,7 +408,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);
-        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, tiles};
+        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles};
         CS_TRY(launch_blend_forward(a, stream), "blend");
     }
     for (int v = 0; v < V; ++v) {
@@ -503,15 +505,15 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
-            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, s->n_tiles};
+            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles};
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_PREPROCESS_BACKWARD, stream);
             PreprocessGrads g{dpoints, ddelta, dsigma, dopacity, dsh};
-            e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->st, s->records, s->counts, grads, g,
-                                           V > 1, stream);
+            e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->scene.sh_degree, s->st, s->records,
+                                           s->counts, grads, g, V > 1, stream);
         }
         if (e != cudaSuccess) st_code = fail_cuda(e, "backward");
     }
@@ -634,7 +636,7 @@ extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, cons
     cudaError_t e = pool_alloc(ctx, (void **)&dc, 12 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 12 * sizeof(unsigned long long), stream);
     const int V = (int)s->views.size();
-    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->st, s->n_tiles};
+    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles};
     if (e == cudaSuccess) e = launch_blend_forward(a, stream, dc);
     if (e == cudaSuccess && dL_dimage && s->n_records) {
         e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);

@@ -189,9 +189,55 @@ __device__ __forceinline__ BlockPos block_pos(const ViewDesc &vd, uint32_t g) {
     return b;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Gathers, into slots sidx[0..nh), the pair indices of up to 32 records whose pixel box meets
+// this warp's 8x4 block, scanning the tile's list from *pos forwards (BACK = false, slots in
+// increasing index order) or backwards from *pos (BACK = true, slots in decreasing order), and
+// advances *pos past what it consumed.  Everything here is warp-uniform except the loads.
+template <bool BACK>
+__device__ __forceinline__ int gather_candidates(const BlendArgs &a, const BlockPos &bp, uint32_t lo, uint32_t hi,
+                                                 uint32_t &pos, uint32_t *sidx, int lane) {
+    const uint32_t lt = lanemask_lt();
+    const float x0 = bp.ox + 0.5f, x1 = bp.ox + 7.5f, y0 = bp.oy + 0.5f, y1 = bp.oy + 3.5f;
+    int nh = 0;
+    while (nh < 32 && (BACK ? pos > lo : pos < hi)) {
+        const uint32_t avail = BACK ? pos - lo : hi - pos;
+        const uint32_t i = BACK ? pos - 1 - (uint32_t)lane : pos + (uint32_t)lane;
+        bool hit = false;
+        if ((uint32_t)lane < avail) {
+            const float4 bb = __ldg(a.bboxes + a.pair_vals[i]);
+            hit = !(bb.z < x0 || bb.x > x1 || bb.w < y0 || bb.y > y1);
+        }
+        const uint32_t hits = __ballot_sync(0xffffffffu, hit);
+        const int room = 32 - nh;
+        uint32_t take = hits;
+        uint32_t consumed = min(32u, avail);
+        if (__popc(hits) > room) {  // keep the first `room` hits and resume after the last one kept
+            take = 0;
+            uint32_t h = hits;
+            for (int k = 0; k < room; ++k) {
+                take |= h & (0u - h);
+                h &= h - 1;
+            }
+            consumed = 32u - (uint32_t)__clz(take);
+        }
+        if ((take >> lane) & 1u) sidx[nh + __popc(take & lt)] = i;
+        nh += __popc(take);
+        pos = BACK ? pos - consumed : pos + consumed;
+    }
+    __syncwarp();
+    return nh;
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[WARPS][32 * SREC];
+    __shared__ uint32_t sidx_all[WARPS][32];
     const uint32_t g = blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
     const BlockPos bp = block_pos(vd, g);
@@ -199,16 +245,18 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
     const Settings st = a.st;
     const int lane = threadIdx.x & 31;
     float4 *wrec = srec[threadIdx.x >> 5];
+    uint32_t *sidx = sidx_all[threadIdx.x >> 5];
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
     bool done = !bp.inside;
     unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
-    for (uint32_t base = range.x; base < range.y; base += 32) {
+    uint32_t pos = range.x;
+    while (pos < range.y) {
         if (__all_sync(0xffffffffu, done)) break;
-        const uint32_t n = min(32u, range.y - base);
+        const int nh = gather_candidates<false>(a, bp, range.x, range.y, pos, sidx, lane);
         bool pass = false;
-        if ((uint32_t)lane < n) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[base + lane], bp.ox, bp.oy, st);
+        if (lane < nh) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], bp.ox, bp.oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         if (!done) {
@@ -226,7 +274,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
                 C1 = fmaf(wgt, c.y, C1);
                 C2 = fmaf(wgt, c.z, C2);
                 T = T * (1.0f - p.alpha);
-                last = base + j + 1;
+                last = sidx[j] + 1;
                 if (T < st.t_min) {
                     done = true;
                     break;
@@ -251,6 +299,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
                                                                   int64_t image_stride, float4 *__restrict__ grads,
                                                                   unsigned long long *counts) {
     __shared__ float4 srec[WARPS][32 * SREC];
+    __shared__ uint32_t sidx_all[WARPS][32];
     const uint32_t g = blockIdx.x;
     const int v = find_view(a.views, a.n_views, g);
     const ViewDesc &vd = a.views[v];
@@ -274,19 +323,20 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
     // colour seen behind the current pair, T_after * (its colour) summed from the back
     float S0 = Tc * st.bg[0], S1 = Tc * st.bg[1], S2 = Tc * st.bg[2];
     unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
+    uint32_t *sidx = sidx_all[threadIdx.x >> 5];
     const uint32_t wend = __reduce_max_sync(0xffffffffu, last);
-    for (uint32_t end = max(wend, range.x); end > range.x;) {
-        const uint32_t start = end > range.x + 32 ? end - 32 : range.x;
-        const uint32_t n = end - start;
+    uint32_t pos = max(wend, range.x);
+    while (pos > range.x) {
+        const int nh = gather_candidates<true>(a, bp, range.x, range.y, pos, sidx, lane);
         bool pass = false;
-        if ((uint32_t)lane < n) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[start + lane], bp.ox, bp.oy, st);
+        if (lane < nh) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], bp.ox, bp.oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
-        while (bits) {  // warp-uniform, from the back of the chunk
-            const int j = 31 - __clz(bits);
-            bits &= ~(1u << j);
+        while (bits) {  // warp-uniform; slots hold decreasing pair indices
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1;
             const float4 *rec = wrec + j * SREC;
-            const uint32_t idx = start + (uint32_t)j;
+            const uint32_t idx = sidx[j];
             PairTerms p;
             const int code = idx < last ? eval_pair(rec, bp.lx, bp.ly, st, p) : -1;
             const bool on = code == 2;
@@ -357,7 +407,6 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
                 atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
         }
         __syncwarp();
-        end = start;
     }
     if (COUNT) flush_counts(counts, cnt);
 }

@@ -39,6 +39,7 @@ struct cs_fwd_state {
     uint32_t *depth_keys = nullptr;
     uint2 *rects = nullptr;
     uint32_t *counts = nullptr;
+    float4 *bboxes = nullptr;
     uint32_t *pair_keys = nullptr, *pair_vals = nullptr;
     uint2 *ranges = nullptr;
     uint32_t *n_last = nullptr;

@@ -63,6 +63,7 @@ struct PreprocessOut {
     uint32_t *depth_keys;  // [R]
     uint2 *rects;          // [R]
     uint32_t *counts;      // [R]
+    float4 *bboxes;        // [R] pixel box (xmin, ymin, xmax, ymax) holding every pixel with alpha >= tau
 };
 cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n,
                               int k, const Settings &st, const PreprocessOut &out, cudaStream_t s);
@@ -70,7 +71,7 @@ cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_h
 struct PreprocessGrads {
     float *dpoints, *ddelta, *dsigma, *dopacity, *dsh;
 };
-cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k,
+cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k, int sh_degree,
                                        const Settings &st, const float4 *records, const uint32_t *counts,
                                        const float4 *grad_records, const PreprocessGrads &g, bool atomic,
                                        cudaStream_t s);
@@ -101,6 +102,7 @@ struct BlendArgs {
     const uint2 *ranges;
     const uint32_t *pair_vals;
     const float4 *records;
+    const float4 *bboxes;
     Settings st;
     uint32_t n_tiles;
 };

@@ -386,6 +386,8 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(const ViewDesc *__re
         int tx0, tx1, ty0, ty1;
         if (full) {
             tx0 = 0; ty0 = 0; tx1 = vd.tiles_x - 1; ty1 = vd.tiles_y - 1;
+            xmin = ymin = -COORD_LIMIT;
+            xmax = ymax = COORD_LIMIT;
         } else {
             tx0 = max((int)floorf(__fmul_rn(xmin, 0.0625f)), 0);
             tx1 = min((int)floorf(__fmul_rn(xmax, 0.0625f)), vd.tiles_x - 1);
@@ -428,6 +430,7 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(const ViewDesc *__re
         float4 *dst = out.records + rec * (REC_WORDS / 4);
 #pragma unroll
         for (int q = 0; q < REC_WORDS / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        out.bboxes[rec] = make_float4(xmin, ymin, xmax, ymax);
         depth_key = __float_as_uint(depth);
         count = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
         rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
@@ -440,164 +443,209 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess(const ViewDesc *__re
 // ---------------------------------------------------------------------------------------------
 // Backward preprocess
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void grad_add(float *p, float v, bool atomic) {
-    if (v == 0.f) return;
-    if (atomic) atomicAdd(p, v);
-    else *p += v;
-}
-
-template <int K>
+// Backward: one thread per drawn convex.  With one view, the points and SH gradients of the
+// block's convexes are accumulated (+=) in shared memory and read / written back with coalesced
+// accesses; with several views, convexes are shared between views and use global atomics.
+template <int K, int DEG, bool ATOMIC>
 __global__ void __launch_bounds__(PRE_THREADS) k_preprocess_backward(const ViewDesc *__restrict__ views, Settings st,
                                                                      const float4 *__restrict__ records,
                                                                      const uint32_t *__restrict__ counts,
                                                                      const float4 *__restrict__ grads,
-                                                                     PreprocessGrads out, bool atomic) {
+                                                                     PreprocessGrads out) {
+    constexpr int NB = (DEG + 1) * (DEG + 1);
+    constexpr int PW = K * 3, SW = NB * 3;           // words per convex
+    constexpr int PS = PW | 1, SS = SW | 1;          // odd strides: no bank conflicts
+    __shared__ float s_dp[ATOMIC ? 1 : PRE_THREADS * PS];
+    __shared__ float s_dsh[ATOMIC ? 1 : PRE_THREADS * SS];
     const ViewDesc &vd = views[blockIdx.y];
-    const int64_t i = (int64_t)blockIdx.x * PRE_THREADS + threadIdx.x;
-    if (i >= vd.n) return;
+    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
+    if (i0 >= vd.n) return;
+    const int cnt = (int)min((int64_t)PRE_THREADS, vd.n - i0);
+    if (!ATOMIC) {
+        if (out.dpoints)
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) s_dp[(q / PW) * PS + q % PW] = out.dpoints[i0 * PW + q];
+        if (out.dsh)
+            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) s_dsh[(q / SW) * SS + q % SW] = out.dsh[i0 * SW + q];
+        __syncthreads();
+    }
+    const int64_t i = i0 + threadIdx.x;
     const int64_t rec = vd.rec_base + i;
-    if (counts[rec] == 0) return;
-    float w[REC_WORDS], gw[GRAD_WORDS];
+    if (i < vd.n && counts[rec] != 0) {
+        float gw[GRAD_WORDS];
+        const float4 h0 = records[rec * (REC_WORDS / 4)], h1 = records[rec * (REC_WORDS / 4) + 1];
 #pragma unroll
-    for (int q = 0; q < REC_WORDS / 4; ++q) {
-        const float4 a = records[rec * (REC_WORDS / 4) + q];
-        const float4 b = grads[rec * (GRAD_WORDS / 4) + q];
-        w[4 * q] = a.x; w[4 * q + 1] = a.y; w[4 * q + 2] = a.z; w[4 * q + 3] = a.w;
-        gw[4 * q] = b.x; gw[4 * q + 1] = b.y; gw[4 * q + 2] = b.z; gw[4 * q + 3] = b.w;
-    }
-    const uint32_t hull = __float_as_uint(w[R_HULL]);
-    const int T = (int)hull_pack_count(hull);
-    const float *P = vd.points + i * K * 3;
-    const float delta = vd.delta[i], sigma = vd.sigma[i];
-    float p[K][3], xc[K][3], u[K], v[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        p[k][0] = P[3 * k];
-        p[k][1] = P[3 * k + 1];
-        p[k][2] = P[3 * k + 2];
-        const float3 x = xform(vd, p[k][0], p[k][1], p[k][2]);
-        xc[k][0] = x.x; xc[k][1] = x.y; xc[k][2] = x.z;
-        u[k] = __fadd_rn(__fmul_rn(vd.fx, __fdiv_rn(x.x, x.z)), vd.cx);
-        v[k] = __fadd_rn(__fmul_rn(vd.fy, __fdiv_rn(x.y, x.z)), vd.cy);
-    }
-    float c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float s = p[0][a];
-#pragma unroll
-        for (int k = 1; k < K; ++k) s = __fadd_rn(s, p[k][a]);
-        c[a] = __fdiv_rn(s, (float)K);
-    }
-    const float3 cc = xform(vd, c[0], c[1], c[2]);
-    const float depth = sqrtf(cc.x * cc.x + cc.y * cc.y + cc.z * cc.z);
-    const float ds = st.dist_mode == 1 ? cc.z : depth;
-    const float g = scale_power(ds, st.dist_power);
-    const float kappa = g * delta * LOG2E;
-
-    // lines -> hull vertices
-    float du[K], dv[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) du[k] = dv[k] = 0.f;
-    float hu[KMAX], hv[KMAX];
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-        if (t < T) select_point<K>(u, v, hull_pack_index(hull, t), hu[t], hv[t]);
-    }
-    const float ax = hu[0], ay = hv[0];
-    float dkappa = 0.f;
-    float dhu[KMAX], dhv[KMAX];
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) dhu[t] = dhv[t] = 0.f;
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-        if (t >= T) break;
-        const int t1 = (t + 1 == T) ? 0 : t + 1;
-        float wx = hu[0], wy = hv[0];
-#pragma unroll
-        for (int q = 1; q < KMAX; ++q)
-            if (q == t1) { wx = hu[q]; wy = hv[q]; }
-        const float ex = wx - hu[t], ey = wy - hv[t];
-        const float len = sqrtf(ex * ex + ey * ey);
-        const float nx = ey / len, ny = -ex / len;
-        const float gA = gw[3 * t], gB = gw[3 * t + 1], gC = gw[3 * t + 2];
-        const float rx = ax - hu[t], ry = ay - hv[t];
-        dkappa += gA * nx + gB * ny + gC * (nx * rx + ny * ry);
-        const float dnx = kappa * (gA + gC * rx), dny = kappa * (gB + gC * ry);
-        dhu[t] -= kappa * gC * nx;
-        dhv[t] -= kappa * gC * ny;
-        const float nd = nx * dnx + ny * dny;
-        const float dux = (dnx - nx * nd) / len, duy = (dny - ny * nd) / len;
-        const float dex = -duy, dey = dux;  // n = (ey, -ex)/|e|
-#pragma unroll
-        for (int q = 0; q < KMAX; ++q)
-            if (q == t1) { dhu[q] += dex; dhv[q] += dey; }
-        dhu[t] -= dex;
-        dhv[t] -= dey;
-    }
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-        if (t >= T) break;
-        const int k = hull_pack_index(hull, t);
-#pragma unroll
-        for (int q = 0; q < K; ++q)
-            if (q == k) { du[q] += dhu[t]; dv[q] += dhv[t]; }
-    }
-    // delta, sigma, scale
-    const float gsig = gw[G_SIG];
-    if (out.ddelta) grad_add(out.ddelta + i, dkappa * g * LOG2E, atomic);
-    if (out.dsigma) grad_add(out.dsigma + i, gsig * g, atomic);
-    if (out.dopacity) grad_add(out.dopacity + i, gw[G_OPA], atomic);
-    const float dg = dkappa * delta * LOG2E + gsig * sigma;
-    float dds;
-    if (st.dist_power == 1.0f) dds = dg;
-    else if (st.dist_power == 0.0f) dds = 0.f;
-    else if (st.dist_power == 0.5f) dds = dg * 0.5f / sqrtf(ds);
-    else dds = dg * 2.f * ds;
-    float dcc[3] = {0.f, 0.f, 0.f};
-    if (st.dist_mode == 1) dcc[2] = dds;
-    else { dcc[0] = dds * cc.x / depth; dcc[1] = dds * cc.y / depth; dcc[2] = dds * cc.z / depth; }
-    float dc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) dc[a] = vd.R[a] * dcc[0] + vd.R[3 + a] * dcc[1] + vd.R[6 + a] * dcc[2];
-    // colour
-    {
-        const int deg = vd.sh_degree, nb = (deg + 1) * (deg + 1);
-        const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
-        const float wl = sqrtf(wx * wx + wy * wy + wz * wz);
-        const float dir[3] = {wx / wl, wy / wl, wz / wl};
-        float Y[16], dY[16][3];
-        sh_eval(deg, dir[0], dir[1], dir[2], Y, dY);
-        const float *sh = vd.sh + i * 3 * nb;
-        float raw[3];
-        sh_colour(sh, deg, Y, raw);
-        float ddir[3] = {0.f, 0.f, 0.f};
-        for (int ch = 0; ch < 3; ++ch) {
-            const float gr = gw[G_RGB + ch];
-            if (!(raw[ch] > 0.f) || gr == 0.f) continue;
-            for (int j = 0; j < nb; ++j) {
-                if (out.dsh) grad_add(out.dsh + (i * nb + j) * 3 + ch, Y[j] * gr, atomic);
-                const float s = sh[3 * j + ch] * gr;
-                ddir[0] += s * dY[j][0];
-                ddir[1] += s * dY[j][1];
-                ddir[2] += s * dY[j][2];
-            }
+        for (int q = 0; q < GRAD_WORDS / 4; ++q) {
+            const float4 b = grads[rec * (GRAD_WORDS / 4) + q];
+            gw[4 * q] = b.x; gw[4 * q + 1] = b.y; gw[4 * q + 2] = b.z; gw[4 * q + 3] = b.w;
         }
-        const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+        (void)h0;
+        const uint32_t hull = __float_as_uint(h1.w);
+        const int T = (int)hull_pack_count(hull);
+        const float *P = vd.points + i * PW;
+        const float delta = vd.delta[i], sigma = vd.sigma[i];
+        float p[K][3], xc[K][3], u[K], v[K];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) dc[a] += (ddir[a] - dir[a] * dd) / wl;
-    }
-    if (!out.dpoints) return;
-    const float invK = 1.0f / (float)K;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const float z = xc[k][2];
-        const float dx = du[k] * vd.fx / z, dy = dv[k] * vd.fy / z;
-        const float dz = -(du[k] * vd.fx * xc[k][0] + dv[k] * vd.fy * xc[k][1]) / (z * z);
+        for (int k = 0; k < K; ++k) {
+            p[k][0] = P[3 * k];
+            p[k][1] = P[3 * k + 1];
+            p[k][2] = P[3 * k + 2];
+            const float3 x = xform(vd, p[k][0], p[k][1], p[k][2]);
+            xc[k][0] = x.x; xc[k][1] = x.y; xc[k][2] = x.z;
+            u[k] = __fadd_rn(__fmul_rn(vd.fx, __fdiv_rn(x.x, x.z)), vd.cx);
+            v[k] = __fadd_rn(__fmul_rn(vd.fy, __fdiv_rn(x.y, x.z)), vd.cy);
+        }
+        float c[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float d = vd.R[a] * dx + vd.R[3 + a] * dy + vd.R[6 + a] * dz + dc[a] * invK;
-            grad_add(out.dpoints + (i * K + k) * 3 + a, d, atomic);
+            float sum = p[0][a];
+#pragma unroll
+            for (int k = 1; k < K; ++k) sum = __fadd_rn(sum, p[k][a]);
+            c[a] = __fdiv_rn(sum, (float)K);
         }
+        const float3 cc = xform(vd, c[0], c[1], c[2]);
+        const float depth = sqrtf(cc.x * cc.x + cc.y * cc.y + cc.z * cc.z);
+        const float ds = st.dist_mode == 1 ? cc.z : depth;
+        const float g = scale_power(ds, st.dist_power);
+        const float kappa = g * delta * LOG2E;
+
+        // lines -> hull vertices -> projected points
+        float hu[KMAX], hv[KMAX];
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t)
+            if (t < T) select_point<K>(u, v, hull_pack_index(hull, t), hu[t], hv[t]);
+        const float ax = hu[0], ay = hv[0];
+        float dkappa = 0.f;
+        float dhu[KMAX], dhv[KMAX];
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) dhu[t] = dhv[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            if (t >= T) break;
+            const int t1 = (t + 1 == T) ? 0 : t + 1;
+            float wx = hu[0], wy = hv[0];
+#pragma unroll
+            for (int q = 1; q < KMAX; ++q)
+                if (q == t1) { wx = hu[q]; wy = hv[q]; }
+            const float ex = wx - hu[t], ey = wy - hv[t];
+            const float len = sqrtf(ex * ex + ey * ey);
+            const float il = 1.0f / len;
+            const float nx = ey * il, ny = -ex * il;
+            const float gA = gw[3 * t], gB = gw[3 * t + 1], gC = gw[3 * t + 2];
+            const float rx = ax - hu[t], ry = ay - hv[t];
+            dkappa += gA * nx + gB * ny + gC * (nx * rx + ny * ry);
+            const float dnx = kappa * (gA + gC * rx), dny = kappa * (gB + gC * ry);
+            dhu[t] -= kappa * gC * nx;
+            dhv[t] -= kappa * gC * ny;
+            const float nd = nx * dnx + ny * dny;
+            const float dux = (dnx - nx * nd) * il, duy = (dny - ny * nd) * il;
+            const float dex = -duy, dey = dux;  // n = (ey, -ex)/|e|
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q)
+                if (q == t1) { dhu[q] += dex; dhv[q] += dey; }
+            dhu[t] -= dex;
+            dhv[t] -= dey;
+        }
+        float du[K], dv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) du[k] = dv[k] = 0.f;
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            if (t >= T) break;
+            const int k = hull_pack_index(hull, t);
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (q == k) { du[q] += dhu[t]; dv[q] += dhv[t]; }
+        }
+        // delta, sigma, opacity, distance
+        const float gsig = gw[G_SIG];
+        const float dd_delta = dkappa * g * LOG2E, dd_sigma = gsig * g, dd_opa = gw[G_OPA];
+        if (ATOMIC) {
+            if (out.ddelta && dd_delta != 0.f) atomicAdd(out.ddelta + i, dd_delta);
+            if (out.dsigma && dd_sigma != 0.f) atomicAdd(out.dsigma + i, dd_sigma);
+            if (out.dopacity && dd_opa != 0.f) atomicAdd(out.dopacity + i, dd_opa);
+        } else {
+            if (out.ddelta) out.ddelta[i] += dd_delta;
+            if (out.dsigma) out.dsigma[i] += dd_sigma;
+            if (out.dopacity) out.dopacity[i] += dd_opa;
+        }
+        const float dg = dkappa * delta * LOG2E + gsig * sigma;
+        float dds;
+        if (st.dist_power == 1.0f) dds = dg;
+        else if (st.dist_power == 0.0f) dds = 0.f;
+        else if (st.dist_power == 0.5f) dds = dg * 0.5f / sqrtf(ds);
+        else dds = dg * 2.f * ds;
+        float dcc[3] = {0.f, 0.f, 0.f};
+        if (st.dist_mode == 1) dcc[2] = dds;
+        else { dcc[0] = dds * cc.x / depth; dcc[1] = dds * cc.y / depth; dcc[2] = dds * cc.z / depth; }
+        float dc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dc[a] = vd.R[a] * dcc[0] + vd.R[3 + a] * dcc[1] + vd.R[6 + a] * dcc[2];
+        // colour: dsh and the gradient of the view direction
+        {
+            const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
+            const float iwl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            const float dir[3] = {wx * iwl, wy * iwl, wz * iwl};
+            float Y[16], dY[16][3];
+            sh_eval(DEG, dir[0], dir[1], dir[2], Y, DEG > 0 ? dY : nullptr);
+            const float *sh = vd.sh + i * SW;
+            float coef[NB][3];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                coef[j][0] = __ldg(sh + 3 * j);
+                coef[j][1] = __ldg(sh + 3 * j + 1);
+                coef[j][2] = __ldg(sh + 3 * j + 2);
+            }
+            float ddir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float raw = 0.5f;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) raw += coef[j][ch] * Y[j];
+                const float gr = (raw > 0.f) ? gw[G_RGB + ch] : 0.f;
+                if (gr == 0.f) continue;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const float d = Y[j] * gr;
+                    if (ATOMIC) {
+                        if (out.dsh) atomicAdd(out.dsh + i * SW + 3 * j + ch, d);
+                    } else {
+                        s_dsh[threadIdx.x * SS + 3 * j + ch] += d;
+                    }
+                    if (DEG > 0) {
+                        const float sg = coef[j][ch] * gr;
+                        ddir[0] += sg * dY[j][0];
+                        ddir[1] += sg * dY[j][1];
+                        ddir[2] += sg * dY[j][2];
+                    }
+                }
+            }
+            const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dc[a] += (ddir[a] - dir[a] * dd) * iwl;
+        }
+        const float invK = 1.0f / (float)K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float iz = 1.0f / xc[k][2];
+            const float dx = du[k] * vd.fx * iz, dy = dv[k] * vd.fy * iz;
+            const float dz = -(du[k] * vd.fx * xc[k][0] + dv[k] * vd.fy * xc[k][1]) * iz * iz;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float d = vd.R[a] * dx + vd.R[3 + a] * dy + vd.R[6 + a] * dz + dc[a] * invK;
+                if (ATOMIC) {
+                    if (out.dpoints && d != 0.f) atomicAdd(out.dpoints + i * PW + 3 * k + a, d);
+                } else {
+                    s_dp[threadIdx.x * PS + 3 * k + a] += d;
+                }
+            }
+        }
+    }
+    if (!ATOMIC) {
+        __syncthreads();
+        if (out.dpoints)
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) out.dpoints[i0 * PW + q] = s_dp[(q / PW) * PS + q % PW];
+        if (out.dsh)
+            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) out.dsh[i0 * SW + q] = s_dsh[(q / SW) * SS + q % SW];
     }
 }
 
@@ -620,24 +668,40 @@ cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k,
+template <int K>
+static void launch_pre_bwd_k(dim3 grid, cudaStream_t s, int deg, bool atomic, const ViewDesc *views_dev,
+                             const Settings &st, const float4 *records, const uint32_t *counts, const float4 *grads,
+                             const PreprocessGrads &g) {
+#define CS_PRE_BWD(D, A) k_preprocess_backward<K, D, A><<<grid, PRE_THREADS, 0, s>>>(views_dev, st, records, counts, grads, g)
+    switch (deg * 2 + (atomic ? 1 : 0)) {
+        case 0: CS_PRE_BWD(0, false); break;
+        case 1: CS_PRE_BWD(0, true); break;
+        case 2: CS_PRE_BWD(1, false); break;
+        case 3: CS_PRE_BWD(1, true); break;
+        case 4: CS_PRE_BWD(2, false); break;
+        case 5: CS_PRE_BWD(2, true); break;
+        case 6: CS_PRE_BWD(3, false); break;
+        default: CS_PRE_BWD(3, true); break;
+    }
+#undef CS_PRE_BWD
+}
+
+cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k, int sh_degree,
                                        const Settings &st, const float4 *records, const uint32_t *counts,
                                        const float4 *grad_records, const PreprocessGrads &g, bool atomic,
                                        cudaStream_t s) {
     if (max_n <= 0 || n_views <= 0) return cudaSuccess;
+    if (sh_degree < 0 || sh_degree > 3) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((max_n + PRE_THREADS - 1) / PRE_THREADS), (unsigned)n_views);
-#define CS_PRE_BWD(KK) \
-    k_preprocess_backward<KK><<<grid, PRE_THREADS, 0, s>>>(views_dev, st, records, counts, grad_records, g, atomic)
     switch (k) {
-        case 3: CS_PRE_BWD(3); break;
-        case 4: CS_PRE_BWD(4); break;
-        case 5: CS_PRE_BWD(5); break;
-        case 6: CS_PRE_BWD(6); break;
-        case 7: CS_PRE_BWD(7); break;
-        case 8: CS_PRE_BWD(8); break;
+        case 3: launch_pre_bwd_k<3>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
+        case 4: launch_pre_bwd_k<4>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
+        case 5: launch_pre_bwd_k<5>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
+        case 6: launch_pre_bwd_k<6>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
+        case 7: launch_pre_bwd_k<7>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
+        case 8: launch_pre_bwd_k<8>(grid, s, sh_degree, atomic, views_dev, st, records, counts, grad_records, g); break;
         default: return cudaErrorInvalidValue;
     }
-#undef CS_PRE_BWD
     count_launches(1);
     return cudaGetLastError();
 }

@@ -107,6 +107,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     uint32_t *depth_keys = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint2 *rects = c.take<uint2>(CS_STATIC_MAX_CONVEXES);
     uint32_t *counts = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
+    float4 *bboxes = c.take<float4>(CS_STATIC_MAX_CONVEXES);
     uint32_t *ka = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *kb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *va = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *vb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *offsets = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
@@ -124,7 +125,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
 
     e = cudaMemcpyAsync(views_dev, &vd, sizeof vd, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
-        PreprocessOut po{records, depth_keys, rects, counts};
+        PreprocessOut po{records, depth_keys, rects, counts, bboxes};
         e = launch_preprocess(views_dev, &vd, 1, R, scene->k, s, po, stream);
     }
     bool in_b = false;
@@ -147,7 +148,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const uint32_t *vals = in_b ? pv2 : pv;
     if (e == cudaSuccess) e = launch_tile_ranges(keys, (int64_t)P, ranges, tiles, stream);  // clears ranges first
     if (e == cudaSuccess) {
-        BlendArgs a{views_dev, 1, ranges, vals, records, s, tiles};
+        BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles};
         e = launch_blend_forward(a, stream);
     }
     if (e != cudaSuccess) return fail_cuda(e, "cs_forward_static");
