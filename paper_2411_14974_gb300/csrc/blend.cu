@@ -1,7 +1,8 @@
 // Per-tile blending of the convex tile rasterizer, forward and backward.
 //
-// One CTA of 256 threads per 16x16 tile; each warp owns an 8x4 pixel block, each thread one
-// pixel, and the warps work independently (no CTA barrier).  A warp walks the tile's
+// Forward: one CTA of 256 threads per 16x16 tile, each warp an 8x4 pixel block, each thread one
+// pixel; backward: 128 threads per tile, each warp an 8x8 block, each thread two pixels (rows r
+// and r + 4).  The warps work independently (no CTA barrier).  A warp walks the tile's
 // depth-ordered records 32 at a time: each lane stages one record in the warp's shared-memory
 // slice (128-byte gather), re-expressed relative to the warp's block origin so that every line
 // is two FMAs per pixel, and tests whether any pixel of the block can pass the line pre-test;
@@ -24,13 +25,15 @@
 namespace cs {
 namespace {
 
-constexpr int BLEND_THREADS = 256;
-constexpr int WARPS = BLEND_THREADS / 32;
-constexpr int SREC = 10;  // float4 per staged record
-// staged record (one per lane of a warp, for that warp's 8x4 pixel block):
+constexpr int FWD_THREADS = 256;  // forward: 8 warps per tile, a warp an 8x4 block, a lane one pixel
+constexpr int BWD_THREADS = 128;  // backward: 4 warps per tile, a warp an 8x8 block, a lane rows r, r + 4
+constexpr int SREC = 11;          // float4 per staged record
+// staged record (one per lane of a warp):
 //   [0] = (sigma', pre-test bound, o, T)   [1] = (r, g, b, record index)
-//   [2 + t] = (A_t, B_t, C_t relative to the block origin, aux); aux of lines 0 and 1 = block
-//   origin minus the record's anchor vertex (x, y), used by the backward
+//   [2] = (block origin minus anchor vertex: x, y, -, -)
+//   [3 + t] = (A_t, B_t, C_t relative to the upper 8x4 block origin, C_t relative to the lower one)
+// The forward's 8x4 blocks and the backward's two 8x4 halves of an 8x8 block are re-based to the
+// same origins, so both kernels evaluate every pair with identical binary32 values.
 constexpr float LN2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float ex2(float x) {
@@ -49,10 +52,12 @@ __device__ __forceinline__ float rcp(float x) {
     return y;
 }
 
-// Stage record r for the 8x4 pixel block whose first pixel centre is (ox + 0.5, oy + 0.5) in
-// image coordinates; lines are re-based to (ox, oy).  Returns false when no pixel of the block
-// can pass the line pre-test: for some line, its smallest value over the block's pixel centres
-// exceeds the bound (with a margin for the per-pixel rounding).
+// Stage record r for the pixel block of 8 x ROWS pixels whose first pixel centre is
+// (ox + 0.5, oy + 0.5) in image coordinates (ROWS = 4: one 8x4 block; ROWS = 8: two stacked 8x4
+// blocks with origins oy and oy + 4).  Returns false when no pixel of the block can pass the
+// line pre-test: for some line, its smallest value over the block's pixel centres exceeds the
+// bound (with a margin for the per-pixel rounding).
+template <int ROWS>
 __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
                                              float oy, const Settings &st) {
     const float4 *src = records + (size_t)r * (REC_WORDS / 4);
@@ -68,7 +73,7 @@ __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restri
             L[4 * q] = L[4 * q + 1] = L[4 * q + 2] = L[4 * q + 3] = 0.f;
         }
     }
-    const float offx = ox - h0.x, offy = oy - h0.y;
+    const float offx = ox - h0.x, offy = oy - h0.y, offy2 = (oy + 4.0f) - h0.y;
     // pre-test: alpha < tau whenever sigma' max_t s_t > log2(o/tau - 1) (phi2 >= max_t s_t); the
     // bound is widened so that it never rejects a pair the full evaluation keeps
     float bound = __int_as_float(0x7f800000);
@@ -85,14 +90,16 @@ __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restri
         if (t < T) {
             const float A = L[3 * t], B = L[3 * t + 1], C = L[3 * t + 2];
             const float Cp = fmaf(A, offx, fmaf(B, offy, C));
-            dst[2 + t] = make_float4(A, B, Cp, t == 0 ? offx : offy);
+            const float Cp2 = ROWS == 8 ? fmaf(A, offx, fmaf(B, offy2, C)) : 0.f;
+            dst[3 + t] = make_float4(A, B, Cp, Cp2);
             const float margin = (fabsf(Cp) + 8.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
-            const float mn = Cp + fminf(0.5f * A, 7.5f * A) + fminf(0.5f * B, 3.5f * B);
+            const float mn = Cp + fminf(0.5f * A, 7.5f * A) + fminf(0.5f * B, ((float)ROWS - 0.5f) * B);
             pass = pass && !(mn > bound + margin);
         }
     }
     dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
     dst[1] = make_float4(h1.x, h1.y, h1.z, __uint_as_float(r));
+    dst[2] = make_float4(offx, offy, 0.f, 0.f);
     return pass;
 }
 
@@ -102,7 +109,9 @@ struct PairTerms {
     float e[KMAX];
 };
 
-// returns 0 when the line pre-test rejects the pair, 1 when alpha < tau, 2 when it contributes
+// returns 0 when the line pre-test rejects the pair, 1 when alpha < tau, 2 when it contributes;
+// HALF selects the 8x4 origin (0 upper, 1 lower) the pixel's local coordinates refer to
+template <int HALF>
 __device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float lx, float ly, const Settings &st,
                                          PairTerms &p) {
     const float4 h0 = rec[0];
@@ -112,8 +121,8 @@ __device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float l
 #pragma unroll
     for (int t = 0; t < KMAX; ++t) {
         if (t < T) {
-            const float4 L = rec[2 + t];
-            s[t] = fmaf(L.x, lx, fmaf(L.y, ly, L.z));
+            const float4 L = rec[3 + t];
+            s[t] = fmaf(L.x, lx, fmaf(L.y, ly, HALF ? L.w : L.z));
             m = fmaxf(m, s[t]);
         }
     }
@@ -165,30 +174,6 @@ __device__ __forceinline__ int find_view(const ViewDesc *__restrict__ views, int
     return v;
 }
 
-// tile coordinates, this thread's pixel and its warp's block origin (image coordinates)
-struct BlockPos {
-    int px, py;        // pixel
-    float ox, oy;      // origin of the warp's 8x4 block
-    float lx, ly;      // pixel centre relative to the block origin
-    bool inside;
-};
-
-__device__ __forceinline__ BlockPos block_pos(const ViewDesc &vd, uint32_t g) {
-    const uint32_t local = g - vd.tile_base;
-    const int tx = (int)(local % (uint32_t)vd.tiles_x), ty = (int)(local / (uint32_t)vd.tiles_x);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
-    BlockPos b;
-    b.px = bx + (lane & 7);
-    b.py = by + (lane >> 3);
-    b.ox = (float)bx;
-    b.oy = (float)by;
-    b.lx = (float)(lane & 7) + 0.5f;
-    b.ly = (float)(lane >> 3) + 0.5f;
-    b.inside = b.px < vd.width && b.py < vd.height;
-    return b;
-}
-
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -196,14 +181,13 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // Gathers, into slots sidx[0..nh), the pair indices of up to 32 records whose pixel box meets
-// this warp's 8x4 block, scanning the tile's list from *pos forwards (BACK = false, slots in
-// increasing index order) or backwards from *pos (BACK = true, slots in decreasing order), and
-// advances *pos past what it consumed.  Everything here is warp-uniform except the loads.
+// the warp's block [x0, x1] x [y0, y1] (pixel centres), scanning the tile's list from pos forwards
+// (BACK = false, slots in increasing index order) or backwards from pos (BACK = true, slots in
+// decreasing order), and advances pos past what it consumed.  Warp-uniform except the loads.
 template <bool BACK>
-__device__ __forceinline__ int gather_candidates(const BlendArgs &a, const BlockPos &bp, uint32_t lo, uint32_t hi,
-                                                 uint32_t &pos, uint32_t *sidx, int lane) {
+__device__ __forceinline__ int gather_candidates(const BlendArgs &a, float x0, float x1, float y0, float y1,
+                                                 uint32_t lo, uint32_t hi, uint32_t &pos, uint32_t *sidx, int lane) {
     const uint32_t lt = lanemask_lt();
-    const float x0 = bp.ox + 0.5f, x1 = bp.ox + 7.5f, y0 = bp.oy + 0.5f, y1 = bp.oy + 3.5f;
     int nh = 0;
     while (nh < 32 && (BACK ? pos > lo : pos < hi)) {
         const uint32_t avail = BACK ? pos - lo : hi - pos;
@@ -234,29 +218,42 @@ __device__ __forceinline__ int gather_candidates(const BlendArgs &a, const Block
     return nh;
 }
 
+__device__ __forceinline__ void tile_of(const ViewDesc &vd, uint32_t g, int &tx, int &ty) {
+    const uint32_t local = g - vd.tile_base;
+    tx = (int)(local % (uint32_t)vd.tiles_x);
+    ty = (int)(local / (uint32_t)vd.tiles_x);
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
-    __shared__ float4 srec[WARPS][32 * SREC];
-    __shared__ uint32_t sidx_all[WARPS][32];
+__global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
+    __shared__ float4 srec[FWD_THREADS / 32][32 * SREC];
+    __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
     const uint32_t g = blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
-    const BlockPos bp = block_pos(vd, g);
+    int tx, ty;
+    tile_of(vd, g, tx, ty);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const bool inside = px < vd.width && py < vd.height;
+    const float ox = (float)bx, oy = (float)by;
+    const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;
     const uint2 range = a.ranges[g];
     const Settings st = a.st;
-    const int lane = threadIdx.x & 31;
-    float4 *wrec = srec[threadIdx.x >> 5];
-    uint32_t *sidx = sidx_all[threadIdx.x >> 5];
+    float4 *wrec = srec[w];
+    uint32_t *sidx = sidx_all[w];
 
     float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t last = 0;
-    bool done = !bp.inside;
-    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
+    bool done = !inside;
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
     uint32_t pos = range.x;
     while (pos < range.y) {
         if (__all_sync(0xffffffffu, done)) break;
-        const int nh = gather_candidates<false>(a, bp, range.x, range.y, pos, sidx, lane);
+        const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, range.x, range.y, pos,
+                                                sidx, lane);
         bool pass = false;
-        if (lane < nh) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], bp.ox, bp.oy, st);
+        if (lane < nh) pass = stage_record<4>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         if (!done) {
@@ -265,7 +262,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
                 bits &= bits - 1;
                 const float4 *rec = wrec + j * SREC;
                 PairTerms p;
-                const int code = eval_pair(rec, bp.lx, bp.ly, st, p);
+                const int code = eval_pair<0>(rec, lx, ly, st, p);
                 if (COUNT) count_pair(cnt, rec, code);
                 if (code != 2) continue;
                 const float4 c = rec[1];
@@ -283,8 +280,8 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
         }
         __syncwarp();
     }
-    if (bp.inside) {
-        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)bp.py * vd.width + bp.px;
+    if (inside) {
+        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)py * vd.width + px;
         vd.image[pix] = fmaf(T, st.bg[0], C0);
         vd.image[hw + pix] = fmaf(T, st.bg[1], C1);
         vd.image[2 * hw + pix] = fmaf(T, st.bg[2], C2);
@@ -295,41 +292,61 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_forward(BlendArgs a, un
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
-                                                                  int64_t image_stride, float4 *__restrict__ grads,
-                                                                  unsigned long long *counts) {
-    __shared__ float4 srec[WARPS][32 * SREC];
-    __shared__ uint32_t sidx_all[WARPS][32];
+__global__ void __launch_bounds__(BWD_THREADS) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
+                                                                int64_t image_stride, float4 *__restrict__ grads,
+                                                                unsigned long long *counts) {
+    __shared__ float4 srec[BWD_THREADS / 32][32 * SREC];
+    __shared__ uint32_t sidx_all[BWD_THREADS / 32][32];
     const uint32_t g = blockIdx.x;
     const int v = find_view(a.views, a.n_views, g);
     const ViewDesc &vd = a.views[v];
-    const BlockPos bp = block_pos(vd, g);
-    const uint2 range = a.ranges[g];
+    int tx, ty;
+    tile_of(vd, g, tx, ty);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 8;
+    const float ox = (float)bx, oy = (float)by;
+    const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;  // within each 8x4 half
+    const int px = bx + (lane & 7);
     const Settings st = a.st;
-    const int lane = threadIdx.x & 31;
-    float4 *wrec = srec[threadIdx.x >> 5];
+    const uint2 range = a.ranges[g];
+    float4 *wrec = srec[w];
+    uint32_t *sidx = sidx_all[w];
 
-    float Tc = 1.0f, G0 = 0.f, G1 = 0.f, G2 = 0.f;
-    uint32_t last = 0;
-    if (bp.inside) {
-        const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)bp.py * vd.width + bp.px;
-        const float *dl = dL_dimage + v * image_stride;
-        G0 = dl[pix];
-        G1 = dl[hw + pix];
-        G2 = dl[2 * hw + pix];
-        Tc = vd.t_final[pix];
-        last = vd.n_last[pix];
+    // pixel k of this lane is row (lane >> 3) of the upper (k = 0) or lower (k = 1) 8x4 half
+    float Tc[2], G0[2], G1[2], G2[2], S0[2], S1[2], S2[2];
+    uint32_t last[2];
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, 0};
+    const size_t hw = (size_t)vd.width * vd.height;
+    const float *dl = dL_dimage + v * image_stride;
+    uint32_t lmax = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int py = by + (lane >> 3) + 4 * k;
+        Tc[k] = 1.0f;
+        G0[k] = G1[k] = G2[k] = 0.f;
+        last[k] = 0;
+        if (px < vd.width && py < vd.height) {
+            const size_t pix = (size_t)py * vd.width + px;
+            G0[k] = dl[pix];
+            G1[k] = dl[hw + pix];
+            G2[k] = dl[2 * hw + pix];
+            Tc[k] = vd.t_final[pix];
+            last[k] = vd.n_last[pix];
+            cnt[5]++;
+        }
+        // colour seen behind the current pair: T_after * (its colour) summed from the back
+        S0[k] = Tc[k] * st.bg[0];
+        S1[k] = Tc[k] * st.bg[1];
+        S2[k] = Tc[k] * st.bg[2];
+        lmax = max(lmax, last[k]);
     }
-    // colour seen behind the current pair, T_after * (its colour) summed from the back
-    float S0 = Tc * st.bg[0], S1 = Tc * st.bg[1], S2 = Tc * st.bg[2];
-    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, bp.inside ? 1ull : 0ull};
-    uint32_t *sidx = sidx_all[threadIdx.x >> 5];
-    const uint32_t wend = __reduce_max_sync(0xffffffffu, last);
+    const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
     uint32_t pos = max(wend, range.x);
     while (pos > range.x) {
-        const int nh = gather_candidates<true>(a, bp, range.x, range.y, pos, sidx, lane);
+        const int nh = gather_candidates<true>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 7.5f, range.x, range.y, pos,
+                                               sidx, lane);
         bool pass = false;
-        if (lane < nh) pass = stage_record(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], bp.ox, bp.oy, st);
+        if (lane < nh) pass = stage_record<8>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         while (bits) {  // warp-uniform; slots hold decreasing pair indices
@@ -337,51 +354,57 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
             bits &= bits - 1;
             const float4 *rec = wrec + j * SREC;
             const uint32_t idx = sidx[j];
-            PairTerms p;
-            const int code = idx < last ? eval_pair(rec, bp.lx, bp.ly, st, p) : -1;
-            const bool on = code == 2;
-            if (COUNT && code >= 0) count_pair(cnt, rec, code);
-            if (!__any_sync(0xffffffffu, on)) continue;
             const float4 h0 = rec[0];
             const int T = __float_as_int(h0.w);
-            // per-pixel terms in gradient-record word order: 3t+0 = g_t lx, 3t+1 = g_t ly,
-            // 3t+2 = g_t, 24 dsigma', 25 dopacity, 26..28 dcolour
+            // per-pixel terms in gradient-record word order, summed over this lane's two pixels
+            // (8x8-block coordinates): 3t+0 = g_t x, 3t+1 = g_t y, 3t+2 = g_t, 24 dsigma',
+            // 25 dopacity, 26..28 dcolour
             float v32[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) v32[q] = 0.f;
-            if (on) {
+            bool any_on = false;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (idx >= last[k]) continue;
+                PairTerms p;
+                const int code = k ? eval_pair<1>(rec, lx, ly, st, p) : eval_pair<0>(rec, lx, ly, st, p);
+                if (COUNT) count_pair(cnt, rec, code);
+                if (code != 2) continue;
+                any_on = true;
                 const float4 c = rec[1];
                 const float om = 1.0f - p.alpha;
                 const float inv = __frcp_rn(om);
-                const float Tn = Tc * inv;  // transmittance in front of this pair
-                const float dalpha =
-                    G0 * (Tn * c.x - S0 * inv) + G1 * (Tn * c.y - S1 * inv) + G2 * (Tn * c.z - S2 * inv);
+                const float Tn = Tc[k] * inv;  // transmittance in front of this pair
+                const float dalpha = G0[k] * (Tn * c.x - S0[k] * inv) + G1[k] * (Tn * c.y - S1[k] * inv) +
+                                     G2[k] * (Tn * c.z - S2[k] * inv);
                 const float ta = Tn * p.alpha;
-                v32[G_RGB] = G0 * ta;
-                v32[G_RGB + 1] = G1 * ta;
-                v32[G_RGB + 2] = G2 * ta;
-                S0 = fmaf(ta, c.x, S0);
-                S1 = fmaf(ta, c.y, S1);
-                S2 = fmaf(ta, c.z, S2);
-                Tc = Tn;
+                v32[G_RGB] += G0[k] * ta;
+                v32[G_RGB + 1] += G1[k] * ta;
+                v32[G_RGB + 2] += G2[k] * ta;
+                S0[k] = fmaf(ta, c.x, S0[k]);
+                S1[k] = fmaf(ta, c.y, S1[k]);
+                S2[k] = fmaf(ta, c.z, S2[k]);
+                Tc[k] = Tn;
                 if (p.oI < st.alpha_max) {
-                    v32[G_OPA] = dalpha * p.I;
+                    v32[G_OPA] += dalpha * p.I;
                     const float dI = dalpha * h0.z;
                     // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
                     const float dx = -dI * LN2 * p.z * p.I * p.I;
-                    v32[G_SIG] = dx * p.phi2;
+                    v32[G_SIG] += dx * p.phi2;
                     const float dphi2 = dx * h0.x * rcp(p.S);
+                    const float ly8 = ly + 4.0f * k;
 #pragma unroll
                     for (int t = 0; t < KMAX; ++t) {
                         if (t < T) {
                             const float gt = dphi2 * p.e[t];
-                            v32[3 * t] = gt * bp.lx;
-                            v32[3 * t + 1] = gt * bp.ly;
-                            v32[3 * t + 2] = gt;
+                            v32[3 * t] = fmaf(gt, lx, v32[3 * t]);
+                            v32[3 * t + 1] = fmaf(gt, ly8, v32[3 * t + 1]);
+                            v32[3 * t + 2] += gt;
                         }
                     }
                 }
             }
+            if (!__any_sync(0xffffffffu, any_on)) continue;
             // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v32[l]
 #pragma unroll
             for (int h = 16; h >= 1; h >>= 1) {
@@ -394,14 +417,14 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
                 }
             }
             float word = v32[0];
-            // s = A (lx + ox - ax) + B (ly + oy - ay) + C: dA = sum(g lx) + (ox - ax) sum(g), dB likewise
+            // s = A (x8 + ox - ax) + B (y8 + oy - ay) + C: dA = sum(g x8) + (ox - ax) sum(g), dB likewise
             const float g2 = __shfl_down_sync(0xffffffffu, word, 2);
             const float g1 = __shfl_down_sync(0xffffffffu, word, 1);
             const uint32_t r = __float_as_uint(rec[1].w);
             if (lane < 24) {
                 const int slot = lane % 3;
-                if (slot == 0) word = fmaf(rec[2].w, g2, word);
-                else if (slot == 1) word = fmaf(rec[3].w, g1, word);
+                if (slot == 0) word = fmaf(rec[2].x, g2, word);
+                else if (slot == 1) word = fmaf(rec[2].y, g1, word);
             }
             if (lane < 29 && word != 0.f)
                 atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
@@ -415,8 +438,8 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_backward(BlendArgs a, c
 
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (counts) k_blend_forward<true><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, counts);
-    else k_blend_forward<false><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, nullptr);
+    if (counts) k_blend_forward<true><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
+    else k_blend_forward<false><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -425,9 +448,9 @@ cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, in
                                   float4 *grad_records, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
     if (counts)
-        k_blend_backward<true><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
+        k_blend_backward<true><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
     else
-        k_blend_backward<false><<<a.n_tiles, BLEND_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
+        k_blend_backward<false><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -243,6 +243,40 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
     }
 }
 
+// One real SH basis function Y_j and its gradient at (x, y, z); j is a constant after unrolling,
+// so only that term's polynomial is evaluated (nothing is kept in arrays).
+__device__ __forceinline__ float sh_term(int j, float x, float y, float z, float &gx, float &gy, float &gz) {
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f;
+    const float C2a = 1.0925484305920792f, C2b = 0.31539156525252005f, C2c = 0.5462742152960396f;
+    const float C3a = 0.5900435899266435f, C3b = 2.890611442640554f, C3c = 0.4570457994644658f;
+    const float C3d = 0.3731763325901154f, C3e = 1.445305721320277f;
+    gx = gy = gz = 0.f;
+    switch (j) {
+        case 0: return C0;
+        case 1: gy = -C1; return -C1 * y;
+        case 2: gz = C1; return C1 * z;
+        case 3: gx = -C1; return -C1 * x;
+        case 4: gx = C2a * y; gy = C2a * x; return C2a * x * y;
+        case 5: gy = -C2a * z; gz = -C2a * y; return -C2a * y * z;
+        case 6: gx = -2.f * C2b * x; gy = -2.f * C2b * y; gz = 4.f * C2b * z; return C2b * (2.f * z * z - x * x - y * y);
+        case 7: gx = -C2a * z; gz = -C2a * x; return -C2a * x * z;
+        case 8: gx = 2.f * C2c * x; gy = -2.f * C2c * y; return C2c * (x * x - y * y);
+        case 9: gx = -6.f * C3a * x * y; gy = -3.f * C3a * (x * x - y * y); return -C3a * y * (3.f * x * x - y * y);
+        case 10: gx = C3b * y * z; gy = C3b * x * z; gz = C3b * x * y; return C3b * x * y * z;
+        case 11:
+            gx = 2.f * C3c * x * y; gy = -C3c * (4.f * z * z - x * x - 3.f * y * y); gz = -8.f * C3c * y * z;
+            return -C3c * y * (4.f * z * z - x * x - y * y);
+        case 12:
+            gx = -6.f * C3d * x * z; gy = -6.f * C3d * y * z; gz = C3d * (6.f * z * z - 3.f * x * x - 3.f * y * y);
+            return C3d * z * (2.f * z * z - 3.f * x * x - 3.f * y * y);
+        case 13:
+            gx = -C3c * (4.f * z * z - 3.f * x * x - y * y); gy = 2.f * C3c * x * y; gz = -8.f * C3c * x * z;
+            return -C3c * x * (4.f * z * z - x * x - y * y);
+        case 14: gx = 2.f * C3e * x * z; gy = -2.f * C3e * y * z; gz = C3e * (x * x - y * y); return C3e * z * (x * x - y * y);
+        default: gx = -3.f * C3a * (x * x - y * y); gy = 6.f * C3a * x * y; return -C3a * x * (x * x - 3.f * y * y);
+    }
+}
+
 // colour = max(0, sum_j sh_j Y_j(dir) + 0.5) per channel; raw values (before the clamp) returned too
 __device__ __forceinline__ void sh_colour(const float *__restrict__ sh, int deg, const float *Y, float raw[3]) {
     const int nb = (deg + 1) * (deg + 1);
@@ -580,48 +614,54 @@ __global__ void __launch_bounds__(PRE_THREADS) k_preprocess_backward(const ViewD
         float dc[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) dc[a] = vd.R[a] * dcc[0] + vd.R[3 + a] * dcc[1] + vd.R[6 + a] * dcc[2];
-        // colour: dsh and the gradient of the view direction
+        // colour: dsh and the gradient of the view direction (basis streamed term by term)
         {
             const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
             const float iwl = rsqrtf(wx * wx + wy * wy + wz * wz);
-            const float dir[3] = {wx * iwl, wy * iwl, wz * iwl};
-            float Y[16], dY[16][3];
-            sh_eval(DEG, dir[0], dir[1], dir[2], Y, DEG > 0 ? dY : nullptr);
+            const float dx = wx * iwl, dy = wy * iwl, dz = wz * iwl;
             const float *sh = vd.sh + i * SW;
-            float coef[NB][3];
+            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
 #pragma unroll
             for (int j = 0; j < NB; ++j) {
-                coef[j][0] = __ldg(sh + 3 * j);
-                coef[j][1] = __ldg(sh + 3 * j + 1);
-                coef[j][2] = __ldg(sh + 3 * j + 2);
+                float gx, gy, gz;
+                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                raw0 += __ldg(sh + 3 * j) * Yj;
+                raw1 += __ldg(sh + 3 * j + 1) * Yj;
+                raw2 += __ldg(sh + 3 * j + 2) * Yj;
             }
-            float ddir[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float raw = 0.5f;
-#pragma unroll
-                for (int j = 0; j < NB; ++j) raw += coef[j][ch] * Y[j];
-                const float gr = (raw > 0.f) ? gw[G_RGB + ch] : 0.f;
-                if (gr == 0.f) continue;
+            const float gr0 = raw0 > 0.f ? gw[G_RGB] : 0.f;
+            const float gr1 = raw1 > 0.f ? gw[G_RGB + 1] : 0.f;
+            const float gr2 = raw2 > 0.f ? gw[G_RGB + 2] : 0.f;
+            float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+            if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
-                    const float d = Y[j] * gr;
+                    float gx, gy, gz;
+                    const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                    const float d0 = Yj * gr0, d1 = Yj * gr1, d2 = Yj * gr2;
                     if (ATOMIC) {
-                        if (out.dsh) atomicAdd(out.dsh + i * SW + 3 * j + ch, d);
+                        if (out.dsh) {
+                            if (d0 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j, d0);
+                            if (d1 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 1, d1);
+                            if (d2 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 2, d2);
+                        }
                     } else {
-                        s_dsh[threadIdx.x * SS + 3 * j + ch] += d;
+                        s_dsh[threadIdx.x * SS + 3 * j] += d0;
+                        s_dsh[threadIdx.x * SS + 3 * j + 1] += d1;
+                        s_dsh[threadIdx.x * SS + 3 * j + 2] += d2;
                     }
                     if (DEG > 0) {
-                        const float sg = coef[j][ch] * gr;
-                        ddir[0] += sg * dY[j][0];
-                        ddir[1] += sg * dY[j][1];
-                        ddir[2] += sg * dY[j][2];
+                        const float sg = __ldg(sh + 3 * j) * gr0 + __ldg(sh + 3 * j + 1) * gr1 + __ldg(sh + 3 * j + 2) * gr2;
+                        ddx += sg * gx;
+                        ddy += sg * gy;
+                        ddz += sg * gz;
                     }
                 }
             }
-            const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) dc[a] += (ddir[a] - dir[a] * dd) * iwl;
+            const float dd = dx * ddx + dy * ddy + dz * ddz;
+            dc[0] += (ddx - dx * dd) * iwl;
+            dc[1] += (ddy - dy * dd) * iwl;
+            dc[2] += (ddz - dz * dd) * iwl;
         }
         const float invK = 1.0f / (float)K;
 #pragma unroll
