@@ -121,12 +121,13 @@ def oracle_sample(sc, cam, npix, seed=0):
     return time.perf_counter() - t0, oracle.num_threads()
 
 
-def serving_bench(dev_index, n_requests=96, seed=0):
+def serving_bench(dev_index, n_requests=192, seed=0):
     """Serving loop: three resident scenes (300k, 1M, 3M convexes), view requests of mixed
     resolution (800x800, 1280x720, 1920x1080) and random poses on spheres of radius 3-5.
-    The batched server (up to 32 views per launch, 32 GB transient budget) and one-view-at-a-time
+    The batched server (8 or 32 views per launch, 32 GB transient budget) and one-view-at-a-time
     serving (max_batch 1) see the same requests: first all at once (capacity), then as a Poisson
-    trace at 80% of the one-at-a-time capacity (latency at equal load)."""
+    trace at 80% of the one-at-a-time capacity (latency at equal load).  Each run first serves a
+    full batch's worth of requests untimed, so the memory pool is warm."""
     import numpy as np
     import torch
     import paper_2411_14974_gb300 as cs
@@ -146,11 +147,13 @@ def serving_bench(dev_index, n_requests=96, seed=0):
     def run(max_batch, arrivals=None):
         with cs.Server(dev_index, budget_bytes=32 << 30, max_batch=max_batch) as srv:
             sids = [srv.add_scene(s) for s in scenes]
-            for i in range(3):  # warm the pool and the kernels
-                srv.submit(sids[i], reqs[0][1], outs[0])
+            nw = max(8, 2 * max_batch)
+            for i in range(nw):  # warm the pool and the kernels with full batches
+                si, cam = reqs[i % len(reqs)]
+                srv.submit(sids[si], cam, outs[i % len(outs)])
             got = 0
-            while got < 3:
-                got += len(srv.poll(16, 100))
+            while got < nw:
+                got += len(srv.poll(256, 100))
             done = []
             t0 = time.perf_counter()
             for i, (si, cam) in enumerate(reqs):
@@ -166,21 +169,22 @@ def serving_bench(dev_index, n_requests=96, seed=0):
             st = srv.stats()
         lat = sorted(d["latency_ms"] for d in done)
         n = len(lat)
-        return dict(p50_ms=lat[n // 2], p99_ms=lat[min(n - 1, int(round(0.99 * (n - 1))))],
+        return dict(max_batch=max_batch, p50_ms=lat[n // 2], p99_ms=lat[min(n - 1, int(round(0.99 * (n - 1))))],
                     views_s=n / (t1 - t0), mean_batch=float(np.mean([d["batch_size"] for d in done])),
                     largest_batch=int(st["largest_batch"]), peak_gb=st["peak_bytes"] / 1e9,
                     ok=all(d["status"] == "ok" for d in done))
 
     cap1 = run(1)
-    capb = run(32)
+    caps = [run(8), run(32)]
+    capb = max(caps, key=lambda c: c["views_s"])
     lam = 0.8 * cap1["views_s"]
     arrivals = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / lam, n_requests))
     load1 = run(1, arrivals)
-    loadb = run(32, arrivals)
+    loadb = run(capb["max_batch"], arrivals)
     return dict(requests=n_requests, scenes=sizes_n, resolutions=["800x800", "1280x720", "1920x1080"],
                 arrival_rate_views_s=lam, p50_ms=loadb["p50_ms"], p99_ms=loadb["p99_ms"],
                 views_s=capb["views_s"], batched_at_load=loadb, one_at_a_time_at_load=load1,
-                batched_capacity=capb, one_at_a_time_capacity=cap1)
+                batched_capacity=caps, one_at_a_time_capacity=cap1)
 
 
 def run_reference(args):

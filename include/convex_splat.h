@@ -142,9 +142,11 @@ typedef enum {
     CS_ARR_DEPTH_KEYS = 1,   /* uint32 [R]: binary32 bits of the camera distance; 0xffffffff if not drawn */
     CS_ARR_RECTS = 2,        /* uint32 [R][2]: tile range (tx0 | tx1 << 16, ty0 | ty1 << 16) */
     CS_ARR_COUNTS = 3,       /* uint32 [R]: number of tiles in the range (0 if not drawn) */
-    CS_ARR_PAIR_KEYS = 4,    /* uint32 [P]: global tile index of each sorted pair */
+    CS_ARR_PAIR_KEYS = 4,    /* uint32 [P]: view << b | tile index within the view, b = bits of the largest
+                                view's tile count (one view: the tile index) */
     CS_ARR_PAIR_VALUES = 5,  /* uint32 [P]: record index (view * N + convex) of each sorted pair */
-    CS_ARR_TILE_RANGES = 6,  /* uint32 [tiles][2]: [start, end) of each tile in the pair list */
+    CS_ARR_TILE_RANGES = 6,  /* uint32 [tiles][2]: [start, end) of each tile in the pair list; tiles of
+                                all views in view order, row major within a view */
     CS_ARR_N_LAST = 7,       /* uint32 [V][H][W]: 1 + pair index of the last contributor, 0 if none */
     CS_ARR_HULLS = 8         /* uint32 [R]: hull size T in bits 0-3, vertex i in bits 4+3i.. */
 } cs_array;

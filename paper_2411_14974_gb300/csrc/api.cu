@@ -314,7 +314,15 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     unsigned long long *scan_tmp = nullptr, *total = nullptr;
     uint64_t P = 0;
     bool in_b = false;
-    const int tile_bits = bits_for(tiles);
+    uint32_t max_view_tiles = 1;
+    for (int v = 0; v < V; ++v) {
+        const uint32_t t = (uint32_t)(s->views[v].tiles_x * s->views[v].tiles_y);
+        max_view_tiles = t > max_view_tiles ? t : max_view_tiles;
+    }
+    const int local_bits = bits_for(max_view_tiles);
+    const int view_bits = bits_for((uint64_t)V);
+    if (local_bits + view_bits > 32) return fail(CS_ERR_ARG, "too many views and tiles for a 32-bit pair key");
+    s->local_bits = local_bits;
 
     CS_TRY(pool_alloc(ctx, (void **)&s->views_dev, sizeof(ViewDesc) * V, stream), "alloc views");
     CS_TRY(pool_alloc(ctx, (void **)&s->records, (size_t)R * REC_WORDS * 4, stream), "alloc records");
@@ -368,8 +376,18 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
                                     &in_b, stream),
                    "depth sort");
         }
-        StageTimer tm(ctx, CS_STAGE_SCAN_EMIT, stream);
         uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;
+        if (V > 1) {
+            // group the depth-ordered records view by view (stable): pairs are then emitted per view
+            StageTimer tv(ctx, CS_STAGE_DEPTH_SORT, stream);
+            uint32_t *vk = in_b ? sort_keys_b : sort_keys_a, *vk2 = in_b ? sort_keys_a : sort_keys_b;
+            uint32_t *vv2 = in_b ? sort_vals_a : sort_vals_b;
+            CS_TRY(launch_view_keys(s->views_dev, V, sorted, R, vk, stream), "view keys");
+            bool vb = false;
+            CS_TRY(radix_sort_pairs(vk, sorted, vk2, vv2, R, view_bits, radix_tmp, scan_tmp, &vb, stream), "view sort");
+            if (vb) sorted = vv2;
+        }
+        StageTimer tm(ctx, CS_STAGE_SCAN_EMIT, stream);
         CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, total, scan_tmp, stream), "scan");
         CS_TRY(cudaMemcpyAsync(ctx->host_total, total, 8, cudaMemcpyDeviceToHost, stream), "read pair count");
         CS_TRY(cudaStreamSynchronize(stream), "synchronize");
@@ -383,8 +401,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
-        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, R, s->pair_keys, s->pair_vals,
-                                 stream),
+        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, R, local_bits, s->pair_keys,
+                                 s->pair_vals, stream),
                "emit pairs");
     }
     // stable sort of the pairs by tile
@@ -397,14 +415,15 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         const int64_t nbk = ((int64_t)P + 4095) / 4096;
         CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words((int64_t)P) * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_tmp_words(256 * (nbk + 1)) * 8, stream), "alloc");
-        CS_TRY(radix_sort_pairs(s->pair_keys, s->pair_vals, pk_b, pv_b, (int64_t)P, tile_bits, radix_tmp, scan_tmp,
+        CS_TRY(radix_sort_pairs(s->pair_keys, s->pair_vals, pk_b, pv_b, (int64_t)P, local_bits, radix_tmp, scan_tmp,
                                 &in_b, stream),
                "tile sort");
         if (in_b) {
             uint32_t *t = s->pair_keys; s->pair_keys = pk_b; pk_b = t;
             t = s->pair_vals; s->pair_vals = pv_b; pv_b = t;
         }
-        CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->ranges, tiles, stream), "tile ranges");
+        CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->views_dev, local_bits, s->ranges, tiles, stream),
+               "tile ranges");
     }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);

@@ -90,11 +90,15 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
                              cudaStream_t s);
 
 cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s);
+// keys[j] = view index of record sorted_records[j]
+cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
+                             uint32_t *keys, cudaStream_t s);
+// pair key = view << local_bits | tile index within the view
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
-                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
-cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, uint2 *ranges, int64_t n_tiles,
-                               cudaStream_t s);
+                              int local_bits, uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
+cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
+                               uint2 *ranges, int64_t n_tiles, cudaStream_t s);
 
 struct BlendArgs {
     const ViewDesc *views;

@@ -4,10 +4,13 @@
 //   1. records sorted by depth key (binary32 bits of the distance, stable, so equal depths keep
 //      increasing record index = convex index within a view);
 //   2. exclusive scan of the per-record tile counts in that order;
-//   3. each record emits (global tile index, record index) pairs, tiles in row-major order;
-//   4. stable radix sort of the pairs by tile index: every tile's list ends up in (depth, index)
-//      order, the same order a single sort on (tile, depth, index) would give;
-//   5. [start, end) range of every tile in the sorted pair list.
+//   3. with several views, a stable pass by view groups the depth-ordered records view by view;
+//   4. each record emits (view << b | tile index within its view, record index) pairs, tiles in
+//      row-major order;
+//   5. stable radix sort of the pairs on the b tile bits only: every (view, tile) group ends up
+//      contiguous and in (depth, index) order, as a single sort on (view, tile, depth, index)
+//      would leave it, with no sort passes spent on the view bits;
+//   6. [start, end) range of every (view, tile) group in the sorted pair list.
 //
 // The radix sort is a three-kernel LSD sort (digit histogram per tile of 4096 keys, scan of the
 // digit-major histogram, stable scatter).  Ranks inside a block come from warp-level key matching
@@ -151,13 +154,20 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
                                                                  const uint32_t *__restrict__ offsets,
                                                                  int64_t nblocks, uint32_t *__restrict__ keys_out,
                                                                  uint32_t *__restrict__ vals_out) {
+    // ranks are stable: warp-striped runs of 32 keys in index order, counted per warp and digit;
+    // the block's keys are then laid out by digit in shared memory so that each digit's run is
+    // written to its global bucket with consecutive addresses
     __shared__ uint32_t cnt[RADIX_WARPS][1 << RADIX_MAX_BITS];
     __shared__ uint32_t gbase[1 << RADIX_MAX_BITS];
+    __shared__ uint32_t lbase[1 << RADIX_MAX_BITS];
+    __shared__ uint32_t skey[RADIX_TILE];
+    __shared__ uint32_t sval[RADIX_TILE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t nbins = 1u << nbits, mask = nbins - 1;
     for (int i = threadIdx.x; i < RADIX_WARPS * (1 << RADIX_MAX_BITS); i += RADIX_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t seg = (int64_t)blockIdx.x * RADIX_TILE + (int64_t)w * (RADIX_ITEMS * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * RADIX_TILE;
+    const int64_t seg = tile0 + (int64_t)w * (RADIX_ITEMS * 32);
     const uint32_t lt = lanemask_lt();
     uint32_t key[RADIX_ITEMS], val[RADIX_ITEMS], dr[RADIX_ITEMS];
 #pragma unroll
@@ -176,24 +186,52 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
         dr[j] = valid ? ((base + __popc(peers & lt)) << 9) | d : 0xffffffffu;
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < nbins; d += RADIX_THREADS) {
-        uint32_t run = 0;
+    // per digit: offsets of the warps inside the block's run of that digit, and the run's total
+    uint32_t total = 0;
+    const uint32_t d_own = threadIdx.x;  // RADIX_THREADS == 256 digits
+    if (d_own < nbins) {
 #pragma unroll
         for (int q = 0; q < RADIX_WARPS; ++q) {
-            const uint32_t c = cnt[q][d];
-            cnt[q][d] = run;
-            run += c;
+            const uint32_t c = cnt[q][d_own];
+            cnt[q][d_own] = total;
+            total += c;
         }
-        gbase[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+        gbase[d_own] = offsets[(int64_t)d_own * nblocks + blockIdx.x];
+    }
+    // block-local start of every digit's run: exclusive scan of the totals over the digits
+    {
+        uint32_t x = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __shared__ uint32_t wsum[RADIX_WARPS];
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        uint32_t wpre = 0;
+#pragma unroll
+        for (int q = 0; q < RADIX_WARPS; ++q)
+            if (q < w) wpre += wsum[q];
+        lbase[d_own] = wpre + x - total;
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < RADIX_ITEMS; ++j) {
         if (dr[j] == 0xffffffffu) continue;
         const uint32_t d = dr[j] & 511u, r = dr[j] >> 9;
-        const uint32_t dst = gbase[d] + cnt[w][d] + r;
-        keys_out[dst] = key[j];
-        vals_out[dst] = val[j];
+        const uint32_t at = lbase[d] + cnt[w][d] + r;
+        skey[at] = key[j];
+        sval[at] = val[j];
+    }
+    __syncthreads();
+    const int nvalid = (int)min((int64_t)RADIX_TILE, n - tile0);
+    for (int i = threadIdx.x; i < nvalid; i += RADIX_THREADS) {
+        const uint32_t k = skey[i];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t dst = gbase[d] + ((uint32_t)i - lbase[d]);
+        keys_out[dst] = k;
+        vals_out[dst] = sval[i];
     }
 }
 
@@ -203,9 +241,22 @@ __global__ void k_iota(uint32_t *v, int64_t n) {
     if (i < n) v[i] = (uint32_t)i;
 }
 
+__device__ __forceinline__ int view_of_record(const ViewDesc *__restrict__ views, int n_views, uint32_t r) {
+    int v = 0;
+    while (v + 1 < n_views && (int64_t)r >= views[v + 1].rec_base) ++v;
+    return v;
+}
+
+__global__ void k_view_keys(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
+                            int64_t n, uint32_t *__restrict__ keys) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) keys[j] = (uint32_t)view_of_record(views, n_views, sorted[j]);
+}
+
+// pair key = view << local_bits | tile index within the view (row major)
 __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
-                       const uint2 *__restrict__ rects, int64_t n_records, uint32_t *__restrict__ keys,
+                       const uint2 *__restrict__ rects, int64_t n_records, int local_bits, uint32_t *__restrict__ keys,
                        uint32_t *__restrict__ vals) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_records) return;
@@ -213,24 +264,26 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
     if (counts[r] == 0) return;
     const uint2 rc = rects[r];
     const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-    int v = 0;
-    while (v + 1 < n_views && (int64_t)r >= views[v + 1].rec_base) ++v;
-    const uint32_t tile_base = views[v].tile_base, tiles_x = (uint32_t)views[v].tiles_x;
+    const int v = view_of_record(views, n_views, r);
+    const uint32_t hi = (uint32_t)v << local_bits, tiles_x = (uint32_t)views[v].tiles_x;
     uint32_t o = offsets[j];
     for (uint32_t ty = ty0; ty <= ty1; ++ty)
         for (uint32_t tx = tx0; tx <= tx1; ++tx) {
-            keys[o] = tile_base + ty * tiles_x + tx;
+            keys[o] = hi | (ty * tiles_x + tx);
             vals[o] = r;
             ++o;
         }
 }
 
-__global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, uint2 *__restrict__ ranges) {
+// [start, end) of every (view, tile) group of the sorted pairs, stored at the global tile index
+__global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, const ViewDesc *__restrict__ views,
+                         int local_bits, uint2 *__restrict__ ranges) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t k = keys[i];
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+    const uint32_t g = views[k >> local_bits].tile_base + (k & ((1u << local_bits) - 1u));
+    if (i == 0 || keys[i - 1] != k) ranges[g].x = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != k) ranges[g].y = (uint32_t)(i + 1);
 }
 
 }  // namespace
@@ -291,21 +344,29 @@ cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
-                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
-                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
-    if (n_records <= 0) return cudaSuccess;
-    k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
-                                                               rects, n_records, pair_keys, pair_vals);
+cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
+                             uint32_t *keys, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_view_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, n, keys);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, uint2 *ranges, int64_t n_tiles,
-                               cudaStream_t s) {
+cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
+                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
+                              int local_bits, uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
+    if (n_records <= 0) return cudaSuccess;
+    k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
+                                                               rects, n_records, local_bits, pair_keys, pair_vals);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
+                               uint2 *ranges, int64_t n_tiles, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
-    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, ranges);
+    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, ranges);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -141,12 +141,13 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     if (P > (unsigned long long)CS_STATIC_MAX_PAIRS)
         return fail(CS_ERR_BUDGET, "cs_forward_static: %llu tile pairs exceed the static limit of %d", P,
                     CS_STATIC_MAX_PAIRS);
-    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, R, pk, pv, stream);
-    if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, bits_for_tiles(tiles), radix_tmp, scan_tmp,
-                                               &in_b, stream);
+    const int local_bits = bits_for_tiles(tiles);
+    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, R, local_bits, pk, pv, stream);
+    if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
+                                               stream);
     const uint32_t *keys = in_b ? pk2 : pk;
     const uint32_t *vals = in_b ? pv2 : pv;
-    if (e == cudaSuccess) e = launch_tile_ranges(keys, (int64_t)P, ranges, tiles, stream);  // clears ranges first
+    if (e == cudaSuccess) e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, ranges, tiles, stream);
     if (e == cudaSuccess) {
         BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles};
         e = launch_blend_forward(a, stream);

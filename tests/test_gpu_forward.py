@@ -40,28 +40,38 @@ def check_discrete(state, sc, cam, rec_base=0, tile_base=0, **kw):
 
 
 def check_pairs(state, discs, cams):
+    """Bit-exact sorted pair list: key = view << b | tile index within the view (b = bits of the
+    largest view's tile count), stable order (tile, view, depth bits, convex index)."""
+    tiles = [((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams]
+    lb = (max(tiles) - 1).bit_length()
     keys, vals = [], []
-    tb, rb = 0, 0
-    for disc, cam in zip(discs, cams):
-        k, v = oracle.sorted_pairs(disc, cam, tb, rb)
-        keys.append(k)
-        vals.append(v)
-        tb += ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    rb = 0
+    for v, (disc, cam) in enumerate(zip(discs, cams)):
+        k, val = oracle.sorted_pairs(disc, cam, 0, rb)
+        keys.append((v << lb) | k)
+        vals.append(val)
         rb += len(disc["visible"])
     keys = np.concatenate(keys)
     vals = np.concatenate(vals)
+    perm = np.argsort(keys & ((1 << lb) - 1), kind="stable")
+    keys, vals = keys[perm], vals[perm]
     gk = state.array("pair_keys").astype(np.int64)
     gv = state.array("pair_values").astype(np.int64)
     assert len(gk) == len(keys), f"{len(gk)} pairs, expected {len(keys)}"
-    assert (gk == keys).all(), "pair tile keys differ"
+    assert (gk == keys).all(), "pair keys differ"
     assert (gv == vals).all(), "pair order differs"
     rng = state.array("tile_ranges").reshape(-1, 2).astype(np.int64)
-    cnt = np.bincount(keys, minlength=tb)
-    nz = cnt > 0
-    assert (rng[nz, 1] - rng[nz, 0] == cnt[nz]).all()
-    assert (rng[~nz] == 0).all()
-    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
-    assert (rng[nz, 0] == starts[nz]).all()
+    base = np.concatenate([[0], np.cumsum(tiles)[:-1]])
+    want = np.zeros((sum(tiles), 2), np.int64)
+    if len(keys):
+        brk = np.nonzero(np.diff(keys))[0] + 1
+        starts = np.concatenate([[0], brk])
+        ends = np.concatenate([brk, [len(keys)]])
+        grp = keys[starts]
+        gidx = base[grp >> lb] + (grp & ((1 << lb) - 1))
+        want[gidx, 0] = starts
+        want[gidx, 1] = ends
+    assert (rng == want).all(), "tile ranges differ"
 
 
 def check_image(img, ref, ill, max_ill=0.02):
