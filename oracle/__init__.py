@@ -69,6 +69,12 @@ def lib():
         _lib.orc_hull2d.argtypes = [P, i32, P]
         _lib.orc_ln_spec.restype = ctypes.c_float
         _lib.orc_ln_spec.argtypes = [ctypes.c_float]
+        _lib.orc_exp_spec.restype = ctypes.c_float
+        _lib.orc_exp_spec.argtypes = [ctypes.c_float]
+        _lib.orc_sigmoid_spec.restype = ctypes.c_float
+        _lib.orc_sigmoid_spec.argtypes = [ctypes.c_float]
+        _lib.orc_activate.restype = None
+        _lib.orc_activate.argtypes = [i64, P, P, P, P, P, P]
         _lib.orc_discrete.restype = ctypes.c_int
         _lib.orc_discrete.argtypes = [P, i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_render_pixels.restype = ctypes.c_int
@@ -122,6 +128,8 @@ def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), di
 
 
 def _scene_arrays(scene):
+    if getattr(scene, "raw", False):
+        raise ValueError("raw-parameter scene: pass activate(scene) to the oracle")
     pts = np.ascontiguousarray(scene.points, np.float32)
     n, k = pts.shape[0], pts.shape[1]
     arr = dict(points=pts,
@@ -148,6 +156,39 @@ def hull2d(uv) -> list:
 
 def ln_spec(x: float) -> float:
     return float(np.float32(lib().orc_ln_spec(np.float32(x))))
+
+
+def exp_spec(x: float) -> float:
+    """The binary32 exp of the parameter activations (Cody-Waite reduction, degree-7 Taylor)."""
+    return float(np.float32(lib().orc_exp_spec(np.float32(x))))
+
+
+def sigmoid_spec(x: float) -> float:
+    return float(np.float32(lib().orc_sigmoid_spec(np.float32(x))))
+
+
+def activate(scene):
+    """Copy of a raw-parameter scene with delta = exp, sigma = exp, opacity = sigmoid of the raw
+    values (Sec. 3.3), each in the binary32 definition both sides share."""
+    n = scene.points.shape[0]
+    rd, rs, ro = (np.ascontiguousarray(getattr(scene, a), np.float32) for a in ("delta", "sigma", "opacity"))
+    d, s, o = np.empty(n, np.float32), np.empty(n, np.float32), np.empty(n, np.float32)
+    lib().orc_activate(n, _p(rd), _p(rs), _p(ro), _p(d), _p(s), _p(o))
+    out = scene.copy()
+    out.delta, out.sigma, out.opacity, out.raw = d, s, o, False
+    return out
+
+
+def raw_gradients(scene_raw, grads: dict) -> dict:
+    """Chain rule from gradients w.r.t. the activated (delta, sigma, opacity) to the raw values:
+    d exp(x)/dx = exp(x), d sigmoid(x)/dx = sigmoid(x) (1 - sigmoid(x)); binary64."""
+    act = activate(scene_raw)
+    out = dict(grads)
+    out["delta"] = grads["delta"] * act.delta.astype(np.float64)
+    out["sigma"] = grads["sigma"] * act.sigma.astype(np.float64)
+    o = act.opacity.astype(np.float64)
+    out["opacity"] = grads["opacity"] * o * (1.0 - o)
+    return out
 
 
 def discrete(scene, cam, st=None) -> dict:

@@ -235,6 +235,55 @@ float orc_ln_spec(float x) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Parameter activations (Sec. 3.3): delta = exp(raw), sigma = exp(raw), o = sigmoid(raw).       */
+/* The activated values decide the tile range, so both sides compute them with one fixed        */
+/* binary32 definition: Cody-Waite reduction x = k ln2 + r with ln2 split into a 16-bit head    */
+/* (k ln2_hi exact for |k| < 256) and a tail, |r| <= ln2/2, then the Taylor polynomial of exp r */
+/* to degree 7 by Horner, scaled by 2^k.  Results below 2^-126 flush to 0, above the binary32   */
+/* range they are +inf.  sigmoid(x) = 1/(1 + exp(-x)).                                         */
+/* ------------------------------------------------------------------------------------------ */
+float orc_exp_spec(float x) {
+    if (x != x) return x;
+    if (x > 88.72283935546875f) return INFINITY;
+    if (x < -87.33654022216797f) return 0.0f;
+    float t = x * 0x1.715476p+0f; /* log2 e */
+    float k = rintf(t);
+    float khi = k * 0x1.62e4p-1f;
+    float klo = k * 0x1.7f7d1cp-20f;
+    float r = x - khi;
+    r = r - klo;
+    float p = 0x1.a01a02p-13f;          /* 1/7! */
+    p = p * r; p = p + 0x1.6c16c2p-10f; /* 1/6! */
+    p = p * r; p = p + 0x1.111112p-7f;  /* 1/5! */
+    p = p * r; p = p + 0x1.555556p-5f;  /* 1/4! */
+    p = p * r; p = p + 0x1.555556p-3f;  /* 1/3! */
+    p = p * r; p = p + 0.5f;
+    p = p * r; p = p + 1.0f;
+    p = p * r; p = p + 1.0f;
+    int ki = (int)k;
+    if (ki > 127) { p = p * 0x1p127f; return p * 2.0f; }
+    union { uint32_t u; float f; } two_k;
+    two_k.u = (uint32_t)(ki + 127) << 23;
+    return p * two_k.f;
+}
+
+float orc_sigmoid_spec(float x) {
+    float e = orc_exp_spec(-x);
+    float den = 1.0f + e;
+    return 1.0f / den;
+}
+
+/* activated (delta, sigma, o) of n convexes from their raw values */
+void orc_activate(int64_t n, const float *raw_delta, const float *raw_sigma, const float *raw_opacity, float *delta,
+                  float *sigma, float *opacity) {
+    for (int64_t i = 0; i < n; i++) {
+        delta[i] = orc_exp_spec(raw_delta[i]);
+        sigma[i] = orc_exp_spec(raw_sigma[i]);
+        opacity[i] = orc_sigmoid_spec(raw_opacity[i]);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Discrete specification of one convex (binary32).                                           */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {

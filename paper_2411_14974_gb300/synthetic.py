@@ -5,9 +5,9 @@ indicator or compositing), so both the CUDA path and the CPU oracle can consume 
 
 Scene layout (all float32, C-contiguous):
   points  [N][K][3]   the K free 3D points of each convex (Sec. 3.2, "point-based representation")
-  delta   [N]         smoothness delta > 0 (Eq. 2), already activated
-  sigma   [N]         sharpness sigma > 0 (Eq. 3), already activated
-  opacity [N]         o in (0, 1) (Eq. 5), already activated
+  delta   [N]         smoothness delta > 0 (Eq. 2), activated unless raw (then log delta)
+  sigma   [N]         sharpness sigma > 0 (Eq. 3), activated unless raw (then log sigma)
+  opacity [N]         o in (0, 1) (Eq. 5), activated unless raw (then logit o)
   sh      [N][(D+1)^2][3]  spherical-harmonic colour coefficients (Sec. 3.2, colour c_n)
 
 Camera: world-to-camera rotation R (row-major 3x3) and translation t with OpenCV axes
@@ -37,6 +37,7 @@ class Scene:
     opacity: np.ndarray
     sh: np.ndarray
     sh_degree: int
+    raw: bool = False  # True: delta, sigma hold log values and opacity its logit (training parameters)
 
     @property
     def n(self) -> int:
@@ -50,11 +51,21 @@ class Scene:
         idx = np.asarray(idx)
         return Scene(np.ascontiguousarray(self.points[idx]), np.ascontiguousarray(self.delta[idx]),
                      np.ascontiguousarray(self.sigma[idx]), np.ascontiguousarray(self.opacity[idx]),
-                     np.ascontiguousarray(self.sh[idx]), self.sh_degree)
+                     np.ascontiguousarray(self.sh[idx]), self.sh_degree, self.raw)
 
     def copy(self) -> "Scene":
         return Scene(self.points.copy(), self.delta.copy(), self.sigma.copy(), self.opacity.copy(),
-                     self.sh.copy(), self.sh_degree)
+                     self.sh.copy(), self.sh_degree, self.raw)
+
+    def as_raw(self) -> "Scene":
+        """The same draw expressed as training parameters: log delta, log sigma, logit opacity
+        (rounded to float32; activating them gives back the drawn values to about an ulp)."""
+        assert not self.raw
+        o = self.opacity.astype(np.float64)
+        f = lambda a: np.ascontiguousarray(a, np.float32)
+        return Scene(self.points.copy(), f(np.log(self.delta.astype(np.float64))),
+                     f(np.log(self.sigma.astype(np.float64))), f(np.log(o) - np.log1p(-o)), self.sh.copy(),
+                     self.sh_degree, True)
 
 
 @dataclasses.dataclass
