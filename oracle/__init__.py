@@ -73,6 +73,8 @@ def lib():
         _lib.orc_exp_spec.argtypes = [ctypes.c_float]
         _lib.orc_sigmoid_spec.restype = ctypes.c_float
         _lib.orc_sigmoid_spec.argtypes = [ctypes.c_float]
+        _lib.orc_ln_array.restype = None
+        _lib.orc_ln_array.argtypes = [i64, P, P]
         _lib.orc_activate.restype = None
         _lib.orc_activate.argtypes = [i64, P, P, P, P, P, P]
         _lib.orc_discrete.restype = ctypes.c_int
@@ -156,6 +158,13 @@ def hull2d(uv) -> list:
 
 def ln_spec(x: float) -> float:
     return float(np.float32(lib().orc_ln_spec(np.float32(x))))
+
+
+def ln_spec_array(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32).ravel()
+    out = np.empty_like(x)
+    lib().orc_ln_array(x.size, _p(x), _p(out))
+    return out
 
 
 def exp_spec(x: float) -> float:

@@ -273,6 +273,11 @@ float orc_sigmoid_spec(float x) {
     return 1.0f / den;
 }
 
+/* ln_spec of n values */
+void orc_ln_array(int64_t n, const float *x, float *out) {
+    for (int64_t i = 0; i < n; i++) out[i] = orc_ln_spec(x[i]);
+}
+
 /* activated (delta, sigma, o) of n convexes from their raw values */
 void orc_activate(int64_t n, const float *raw_delta, const float *raw_sigma, const float *raw_opacity, float *delta,
                   float *sigma, float *opacity) {

@@ -90,3 +90,98 @@ def adam_step(p, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-15):
     mhat = m / (1.0 - beta1 ** t)
     vhat = v / (1.0 - beta2 ** t)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# ---- adaptive refinement: K-way split and pruning (Sec. 3.3, supplement Sec. A) ----------------
+def _centre32(points32: np.ndarray) -> np.ndarray:
+    """Mean of the K points in binary32: sequential sum over k, then divide by K."""
+    f32 = np.float32
+    s = points32[:, 0, :].copy()
+    for k in range(1, points32.shape[1]):
+        s = (s + points32[:, k, :]).astype(f32)
+    return (s / f32(points32.shape[1])).astype(f32)
+
+
+def densify_decisions(points, opacity_raw, sigma_grad_abs, window_steps, threshold=4e-6, prune_opacity=0.03,
+                      prune_size=np.inf):
+    """Per convex 0 = keep, 1 = split, 2 = prune, all decided in binary32.
+
+    Prune (checked first) when the activated opacity is below prune_opacity or the convex's size,
+    the largest distance from its centre to one of its points, exceeds prune_size (supplement
+    Sec. A: opacity < 0.03, size > 0.3 x scene size).  Otherwise split when the sharpness statistic,
+    the mean |dL/dsigma| over the steps since the last refinement, exceeds the threshold (the
+    paper's "loss of sigma exceeds 0.000004").  Non-finite values prune."""
+    f32 = np.float32
+    p = np.ascontiguousarray(points, f32)
+    c = _centre32(p)
+    d = (p - c[:, None, :]).astype(f32)
+    size = np.sqrt(((d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]).astype(f32) + d[..., 2] * d[..., 2]).astype(f32))
+    size = size.max(axis=1)
+    o = _sigmoid_vec(opacity_raw)
+    mean = (np.ascontiguousarray(sigma_grad_abs, f32) / f32(window_steps)).astype(f32)
+    prune = ~(o >= f32(prune_opacity)) | ~(size <= f32(prune_size))
+    split = ~prune & (mean > f32(threshold))
+    return np.where(prune, 2, np.where(split, 1, 0)).astype(np.int32)
+
+
+def _sigmoid_vec(raw32):
+    """sigmoid_spec of every value (the oracle's binary32 activation, evaluated in C)."""
+    import oracle
+    raw32 = np.ascontiguousarray(raw32, np.float32)
+    n = raw32.size
+    z = np.zeros(n, np.float32)
+    d, s, o = (np.empty(n, np.float32) for _ in range(3))
+    oracle.lib().orc_activate(n, oracle._p(z), oracle._p(z), oracle._p(raw32), oracle._p(d), oracle._p(s),
+                              oracle._p(o))
+    return o
+
+
+def densify(params: dict, m: dict, v: dict, sigma_grad_abs, window_steps, threshold=4e-6, split_scale=0.7,
+            split_sigma_scale=1.5, split_opacity_scale=0.5, prune_opacity=0.03, prune_size=np.inf):
+    """Refined raw-parameter set (points, delta, sigma, opacity, sh as log/logit values) and Adam
+    moments, in binary32.  Output order: for each input convex in order, itself when kept, its K
+    children when split, nothing when pruned.  Child j of a convex with points p_k and centre c
+    has points p_j + s (p_k - c) (scaled down by s about its new centre p_j), the same delta and
+    colour, sigma x split_sigma_scale (raw: + ln scale) and opacity x split_opacity_scale (raw:
+    ln(o'/(1 - o'))), ln being the binary32 definition shared with the tile range; its moments
+    start at 0.  Returns (params, m, v, decisions)."""
+    import oracle
+    f32 = np.float32
+    P = {k: np.ascontiguousarray(params[k], f32) for k in ("points", "delta", "sigma", "opacity", "sh")}
+    dec = densify_decisions(P["points"], P["opacity"], sigma_grad_abs, window_steps, threshold, prune_opacity,
+                            prune_size)
+    N, K = P["points"].shape[:2]
+    c = _centre32(P["points"])
+    d = (P["points"] - c[:, None, :]).astype(f32)
+    o = _sigmoid_vec(P["opacity"])
+    oc = (o * f32(split_opacity_scale)).astype(f32)
+    ratio = (oc / (f32(1.0) - oc).astype(f32)).astype(f32)
+    child_op = oracle.ln_spec_array(ratio)
+    ln_ss = f32(oracle.ln_spec(float(f32(split_sigma_scale))))
+    child_sig = (P["sigma"] + ln_ss).astype(f32)
+    out = {k: [] for k in P}
+    om = {k: [] for k in P}
+    ov = {k: [] for k in P}
+    for i in range(N):
+        if dec[i] == 2:
+            continue
+        if dec[i] == 0:
+            for k in P:
+                out[k].append(P[k][i:i + 1])
+                om[k].append(np.ascontiguousarray(m[k], f32)[i:i + 1])
+                ov[k].append(np.ascontiguousarray(v[k], f32)[i:i + 1])
+            continue
+        for j in range(K):
+            pts = (P["points"][i, j][None, :] + (f32(split_scale) * d[i]).astype(f32)).astype(f32)
+            out["points"].append(pts[None])
+            out["delta"].append(P["delta"][i:i + 1])
+            out["sigma"].append(child_sig[i:i + 1])
+            out["opacity"].append(child_op[i:i + 1])
+            out["sh"].append(P["sh"][i:i + 1])
+            for k in P:
+                om[k].append(np.zeros_like(P[k][i:i + 1]))
+                ov[k].append(np.zeros_like(P[k][i:i + 1]))
+
+    def cat(lst, k):
+        return np.concatenate(lst, 0) if lst else np.zeros((0,) + P[k].shape[1:], f32)
+    return ({k: cat(out[k], k) for k in P}, {k: cat(om[k], k) for k in P}, {k: cat(ov[k], k) for k in P}, dec)

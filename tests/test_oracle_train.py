@@ -110,3 +110,75 @@ def test_adam_matches_torch_optim_adam():
         opt.step()
         p, m, v = T.adam_step(p, gr, m, v, lr=0.005, t=t, eps=1e-8)
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+# ---- adaptive refinement (split / prune) --------------------------------------------------------
+def _raw_params(n, seed=0, k=6, deg=1):
+    from paper_2411_14974_gb300 import synthetic as syn
+    r = syn.blob_scene(seed, n=n, k=k, sh_degree=deg).as_raw()
+    return dict(points=r.points, delta=r.delta, sigma=r.sigma, opacity=r.opacity, sh=r.sh)
+
+
+def _zeros_like(P):
+    return {k: np.zeros_like(v) for k, v in P.items()}
+
+
+def test_densify_with_nothing_to_do_is_the_identity():
+    P = _raw_params(40)
+    M = {k: np.random.default_rng(1).normal(size=v.shape).astype(np.float32) for k, v in P.items()}
+    out, m, v, dec = T.densify(P, M, M, np.zeros(40, np.float32), 10, threshold=1.0, prune_opacity=0.0)
+    assert (dec == 0).all()
+    for k in P:
+        np.testing.assert_array_equal(out[k], P[k])
+        np.testing.assert_array_equal(m[k], M[k])
+
+
+def test_split_children_follow_the_paper():
+    """K children centred at the parent's points, offsets scaled by s, same delta and colour,
+    sigma x 1.5 and opacity x 0.5 after activation, zero moments."""
+    import oracle
+    P = _raw_params(3, seed=2, k=5)
+    acc = np.array([0.0, 1.0, 0.0], np.float32)  # only convex 1 splits
+    out, m, v, dec = T.densify(P, _zeros_like(P), _zeros_like(P), acc, 1, threshold=0.5, split_scale=0.6,
+                               prune_opacity=0.0)
+    assert dec.tolist() == [0, 1, 0]
+    assert out["points"].shape[0] == 2 + 5
+    parent = P["points"][1].astype(np.float64)
+    c = parent.mean(axis=0)
+    for j in range(5):
+        child = out["points"][1 + j].astype(np.float64)
+        np.testing.assert_allclose(child.mean(axis=0), parent[j], atol=1e-6)
+        np.testing.assert_allclose(child - child.mean(axis=0), 0.6 * (parent - c), atol=1e-6)
+        assert out["delta"][1 + j] == P["delta"][1]
+        np.testing.assert_array_equal(out["sh"][1 + j], P["sh"][1])
+        s_parent = math.exp(float(P["sigma"][1]))
+        assert abs(math.exp(float(out["sigma"][1 + j])) - 1.5 * s_parent) <= 1e-6 * s_parent
+        o_parent = 1.0 / (1.0 + math.exp(-float(P["opacity"][1])))
+        o_child = 1.0 / (1.0 + math.exp(-float(out["opacity"][1 + j])))
+        assert abs(o_child - 0.5 * o_parent) <= 1e-6
+        for k in P:
+            assert not m[k][1 + j].any() and not v[k][1 + j].any()
+    np.testing.assert_array_equal(out["points"][0], P["points"][0])
+    np.testing.assert_array_equal(out["points"][-1], P["points"][2])
+
+
+def test_prune_by_opacity_and_size_and_nonfinite():
+    P = _raw_params(6, seed=3)
+    P["opacity"][0] = -5.0                              # sigmoid ~ 0.0067 < 0.03
+    P["opacity"][1] = float(np.log(0.031 / 0.969))      # just above 0.03: kept
+    P["points"][2] = P["points"][2] * 0 + np.array([0.0, 0.0, 0.0], np.float32)
+    P["points"][2][0] = [1.0, 0.0, 0.0]                 # size about 0.83 > 0.5
+    P["points"][3][0, 0] = np.nan
+    acc = np.full(6, 1.0, np.float32)                   # everything else would split
+    out, m, v, dec = T.densify(P, _zeros_like(P), _zeros_like(P), acc, 1, threshold=0.5, prune_size=0.5)
+    assert dec.tolist()[:4] == [2, 1, 2, 2]
+    assert out["points"].shape[0] == 6 * int((dec == 1).sum())
+
+
+def test_split_decision_is_strictly_greater_in_binary32():
+    P = _raw_params(3, seed=4)
+    thr = np.float32(4e-6)
+    acc = np.array([thr * 8, np.nextafter(thr, np.float32(1)) * 8, np.nextafter(thr, np.float32(0)) * 8],
+                   np.float32)
+    dec = T.densify_decisions(P["points"], P["opacity"], acc, 8, threshold=float(thr), prune_opacity=0.0)
+    assert dec.tolist() == [0, 1, 0]
