@@ -187,6 +187,205 @@ def serving_bench(dev_index, n_requests=192, seed=0):
                 batched_capacity=caps, one_at_a_time_capacity=cap1)
 
 
+def tile_test_bench(dev_index, sc, cams, steps, warmup):
+    """The main step with the exact tile test on (tile_test = 1): ms, stage split and pairs."""
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    dev = torch.device("cuda", dev_index)
+    scene = cs.SceneTensors.from_numpy(sc, dev)
+    H, W = cams[0].height, cams[0].width
+    dL = torch.as_tensor(np.random.default_rng(1).uniform(-1, 1, (1, 3, H, W)).astype(np.float32), device=dev)
+    grads = {k: torch.zeros_like(getattr(scene, k)) for k in cs.PARAMS}
+    image = torch.empty((1, 3, H, W), device=dev)
+    out = {}
+    for tt in (0, 1):
+        settings = cs.Settings(tile_test=tt)
+
+        def step(i):
+            _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
+            cs.backward(st, dL, grads)
+            st.release()
+
+        for i in range(warmup):
+            step(i)
+        torch.cuda.synchronize()
+        cs.profile_enable(True, dev_index)
+        cs.profile_read(dev_index)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        stages = cs.profile_read(dev_index)
+        cs.profile_enable(False, dev_index)
+        _, _, st = cs.forward(scene, [cams[0]], settings, keep_state=True, image=image)
+        pairs = st.sizes()["pairs"]
+        st.release()
+        out[f"tile_test_{tt}"] = dict(ms_per_step=e0.elapsed_time(e1) / steps, pairs_view0=pairs,
+                                      breakdown_ms={k: v[0] / steps for k, v in stages.items() if v[0] > 0})
+    return out
+
+
+def light_bench(dev_index, sc, cams, steps, warmup):
+    """The same scene and views with the parameters stored in binary16 (the paper's light model):
+    forward and forward + backward ms and the stage split; the preprocess reads half the bytes."""
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    dev = torch.device("cuda", dev_index)
+    scene = cs.SceneTensors.from_numpy(sc, dev, dtype=torch.float16)
+    H, W = cams[0].height, cams[0].width
+    dL = torch.as_tensor(np.random.default_rng(1).uniform(-1, 1, (1, 3, H, W)).astype(np.float32), device=dev)
+    grads = {k: torch.zeros(getattr(scene, k).shape, device=dev) for k in cs.PARAMS}
+    image = torch.empty((1, 3, H, W), device=dev)
+    settings = cs.Settings()
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for i in range(warmup):
+            fn(i)
+        torch.cuda.synchronize()
+        cs.profile_enable(True, dev_index)
+        cs.profile_read(dev_index)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            fn(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = cs.profile_read(dev_index)
+        cs.profile_enable(False, dev_index)
+        return e0.elapsed_time(e1) / steps, {k: v[0] / steps for k, v in st.items() if v[0] > 0}
+
+    def fwd(i):
+        cs.forward(scene, [cams[i % len(cams)]], settings, image=image)
+
+    def fwd_bwd(i):
+        _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
+        cs.backward(st, dL, grads)
+        st.release()
+
+    f_ms, f_bd = timed(fwd)
+    fb_ms, fb_bd = timed(fwd_bwd)
+    return dict(storage="float16", fwd_ms=f_ms, fwd_mpix_s=H * W / (f_ms / 1e3) / 1e6, fwd_bwd_ms=fb_ms,
+                fwd_bwd_mpix_s=H * W / (fb_ms / 1e3) / 1e6, breakdown_ms=fb_bd,
+                param_bytes=int(sum(getattr(scene, k).numel() * 2 for k in cs.PARAMS)))
+
+
+def train_bench(dev_index, sc, cams, steps, warmup):
+    """Training iteration of Sec. 3.3 on the same scene as raw parameters (log delta, log sigma,
+    logit opacity): forward with the activations in the preprocess, L1 + D-SSIM (lambda 0.2)
+    against a U[0,1] target, backward to the raw parameters, one fused Adam launch over all five
+    groups.  Views cycle as in the main step; ms/iter and the per-stage split."""
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    dev = torch.device("cuda", dev_index)
+    scene = cs.SceneTensors.from_numpy(sc.as_raw(), dev)
+    H, W = cams[0].height, cams[0].width
+    target = torch.as_tensor(np.random.default_rng(9).uniform(0, 1, (1, 3, H, W)).astype(np.float32), device=dev)
+    tr = cs.Trainer(scene)
+    for i in range(warmup):
+        tr.step([cams[i % len(cams)]], target)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    cs.profile_enable(True, dev_index)
+    cs.profile_read(dev_index)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        tr.step([cams[i % len(cams)]], target)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stages = cs.profile_read(dev_index)
+    cs.profile_enable(False, dev_index)
+    ms = e0.elapsed_time(e1) / steps
+    n_params = sum(getattr(scene, k).numel() for k in cs.PARAMS)
+    opt_ms = stages["optimizer"][0] / steps
+    return dict(ms_per_iter=ms, steps=steps, loss=float(tr.loss.item()),
+                breakdown_ms={k: v[0] / steps for k, v in stages.items()},
+                optimizer_gbs=n_params * 32 / (opt_ms / 1e3) / 1e9 if opt_ms > 0 else None,
+                optimizer_bytes_per_param=32, params=int(n_params))
+
+
+def stress_bench(dev_index, steps=3, warmup=2, tile_test=0):
+    """Load balance under heavy clustering: 3M convexes with 90% of the centres in 5% of the
+    volume, 16 views of 3840x2160 (518,400 tiles) binned, sorted and blended in one batch, forward
+    and backward.  Reports ms per step, the stage split, pairs per tile (max / mean / CV) and the
+    blend's MUFU and FP32 fractions from the instrumented work counts."""
+    import numpy as np
+    import torch
+    import paper_2411_14974_gb300 as cs
+    from paper_2411_14974_gb300 import synthetic as syn
+    dev = torch.device("cuda", dev_index)
+    sc, cams = syn.workload("clustered3M_3840x2160x16", seed=0)
+    scene = cs.SceneTensors.from_numpy(sc, dev)
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    gen = torch.Generator(device=dev).manual_seed(11)
+    dL = torch.rand((V, 3, H, W), device=dev, generator=gen) * 2 - 1
+    image = torch.empty((V, 3, H, W), device=dev)
+    grads = {k: torch.zeros_like(getattr(scene, k)) for k in cs.PARAMS}
+    settings = cs.Settings(tile_test=tile_test)
+
+    def step():
+        _, _, st = cs.forward(scene, cams, settings, keep_state=True, image=image)
+        cs.backward(st, dL, grads)
+        return st
+
+    for _ in range(warmup):
+        step().release()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    cs.profile_enable(True, dev_index)
+    cs.profile_read(dev_index)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step().release()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stages = cs.profile_read(dev_index)
+    cs.profile_enable(False, dev_index)
+    ms = e0.elapsed_time(e1) / steps
+    _, _, st = cs.forward(scene, cams, settings, keep_state=True, image=image)
+    sizes = st.sizes()
+    rng = st.array("tile_ranges").reshape(-1, 2).astype(np.int64)
+    per_tile = rng[:, 1] - rng[:, 0]
+    wc = cs.work_counts(st, dL)
+    st.release()
+    bd = {k: v[0] / steps for k, v in stages.items()}
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mufu_peak = sm * 16 * 2070e6
+    fp32_peak = sm * 128 * 2070e6
+    frac = {}
+    for name, key, extra in (("blend", "forward", 0), ("blend_backward", "backward", 2)):
+        w = wc[key]
+        t = bd[name] / 1e3
+        mufu = w["lines_passed"] + 3 * w["passed"] + extra * w["contributing"]
+        fp32 = 3 * w["lines_visited"] + 2 * w["lines_passed"] + 12 * w["passed"]
+        frac[name] = dict(mufu_frac=mufu / t / mufu_peak, fp32_frac=fp32 / t / fp32_peak)
+    pre_bytes = V * sc.n * (276 + 144)
+    frac["preprocess"] = dict(hbm_frac=pre_bytes / (bd["preprocess"] / 1e3) / 1e9 / _hbm_peak())
+    return dict(workload="clustered3M_3840x2160x16", views=V, tile_test=tile_test, ms_per_step=ms,
+                mpix_s=V * H * W / (ms / 1e3) / 1e6, breakdown_ms=bd, records=sizes["records"],
+                pairs=sizes["pairs"], tiles=sizes["tiles"],
+                pairs_per_tile=dict(max=int(per_tile.max()), mean=float(per_tile.mean()),
+                                    cv=float(per_tile.std() / max(per_tile.mean(), 1e-9)),
+                                    empty_frac=float((per_tile == 0).mean())),
+                evaluated_pairs=wc["forward"]["passed"], fractions_at_2070mhz=frac)
+
+
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the host cores (rank 0 only)."""
     ws, rank, _ = dist_env()
@@ -356,6 +555,16 @@ def run_ours(args):
         d2h = host_img.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
         out["e2e"] = dict(value=pixels_per_step / e2e_s / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
                           d2h_bytes_per_step=int(d2h), ms_per_step=e2e_s * 1e3)
+        # 16-bit parameter storage (the light model) on the same scene and views
+        out["light16"] = light_bench(local, sc, cams, max(args.steps, 5), 3)
+        # training iteration (raw parameters, loss, Adam) on the same scene and views
+        out["train_step"] = train_bench(local, sc, cams, max(args.steps, 5), 3)
+        # the exact tile test on and off, on this workload and on the clustered 4K batch
+        out["tile_test"] = tile_test_bench(local, sc, cams, max(args.steps, 5), 3)
+        # heavy clustering, 16 views of 4K in one batch: per-tile load
+        out["stress"] = stress_bench(local)
+        out["tile_test"]["stress_tile_test_1"] = {k: v for k, v in stress_bench(local, tile_test=1).items()
+                                                  if k in ("ms_per_step", "pairs", "pairs_per_tile", "breakdown_ms")}
         # serving loop (continuous batching) against one-view-at-a-time on the same requests
         out["serving"] = serving_bench(local)
         # CPU oracle on a bounded sample of the same workload

@@ -70,7 +70,7 @@ typedef struct {
 
 /* Compositing constants.  The paper's Eq. 5 has none; these follow the 3DGS tile rasterizer the
    paper builds on (Sec. 3.2).  cs_default_settings(): tau = 1/255, alpha_max = 0.99,
-   t_min = 1e-4, bg = 0, dist_mode = 0, dist_power = 1. */
+   t_min = 1e-4, bg = 0, dist_mode = 0, dist_power = 1, tile_test = 0. */
 typedef struct {
     float tau;          /* pairs with alpha < tau add nothing; 0 <= tau < 1 */
     float alpha_max;    /* alpha = min(alpha_max, o I); 0 < alpha_max <= 1 */
@@ -78,20 +78,47 @@ typedef struct {
     float bg[3];        /* background colour added with the final transmittance */
     int32_t dist_mode;  /* d = |R c + t| (0) or the camera z of c (1); c = mean of the K points */
     float dist_power;   /* delta, sigma scaled by d^p, p in {0, 0.5, 1, 2} (supp. Sec. C ablation) */
+    int32_t tile_test;  /* 0: a convex covers every tile of its conservative rectangle; 1: only the
+                           tiles an exact separating-axis test against its offset hull keeps (fewer
+                           pairs, more work per convex; see the tile-range notes of cs_forward) */
 } cs_settings;
 
-/* A scene: device pointers to N convexes with K points each (3 <= K <= 8) and SH degree D (0..3).
-   delta, sigma > 0 and opacity in (0, 1] are activated values (the paper activates with exp and
-   sigmoid, Sec. 3.3).  Convexes with non-finite or non-positive delta/sigma are not drawn. */
+/* How delta, sigma and opacity are given (Sec. 3.3 optimises them through activations). */
+typedef enum {
+    CS_ACT_NONE = 0,         /* activated values: delta, sigma > 0, opacity in (0, 1] */
+    CS_ACT_EXP_SIGMOID = 1   /* training parameters: delta = exp(x), sigma = exp(x), opacity = sigmoid(x)
+                                of the stored x, applied inside the forward; the backward then returns
+                                gradients with respect to the stored x.  exp is one fixed binary32
+                                definition (Cody-Waite reduction with ln 2 split into a 16-bit head
+                                and a tail, degree-7 Taylor polynomial by Horner, times 2^k; 0 below
+                                2^-126, +inf above the binary32 range), sigmoid(x) = 1/(1 + exp(-x)) */
+} cs_activation;
+
+/* Element type of a scene's parameter arrays.  The 16-bit formats are the paper's "light" model
+   storage (Sec. 4.2, supplement Sec. A: weights stored in 16-bit precision); every value is
+   widened to binary32 on load and all arithmetic is binary32, so a 16-bit scene renders exactly
+   like the binary32 scene holding the same (widened) values.  Gradients are always float32. */
+typedef enum {
+    CS_STORE_F32 = 0,
+    CS_STORE_F16 = 1,   /* IEEE binary16 */
+    CS_STORE_BF16 = 2   /* bfloat16 */
+} cs_storage;
+
+/* A scene: device pointers to N convexes with K points each (3 <= K <= 8) and SH degree D (0..3),
+   every array of the element type `storage`: points [N][K][3], delta [N], sigma [N], opacity [N],
+   sh [N][(D+1)^2][3].  Convexes whose (activated) delta/sigma are non-finite or non-positive are
+   not drawn. */
 typedef struct {
-    const float *points;
-    const float *delta;
-    const float *sigma;
-    const float *opacity;
-    const float *sh;
+    const void *points;
+    const void *delta;
+    const void *sigma;
+    const void *opacity;
+    const void *sh;
     int64_t n;
     int32_t k;
     int32_t sh_degree;
+    int32_t activation;   /* cs_activation */
+    int32_t storage;      /* cs_storage */
 } cs_scene;
 
 typedef struct cs_context cs_context;      /* per-device library state: stream-ordered memory pool */
@@ -191,6 +218,94 @@ cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_cam
 cs_status cs_forward_static(const cs_scene *scene, const cs_camera *cam, const cs_settings *settings, float *image,
                             float *t_final, void *stream);
 
+/* ---- training step around the renderer (Sec. 3.3) --------------------------------------------
+   With scene.activation = CS_ACT_EXP_SIGMOID the forward/backward above work on the training
+   parameters directly; these two calls add the loss and the optimiser, all on the device. */
+
+/* Photometric loss of Sec. 3.3 (Eq. 6 without the mask term, lambda = 0.2 in the paper):
+     L = (1 - lambda) mean|image - target| + lambda (1 - mean SSIM(image, target))
+   over n_views x 3 x height x width elements (layout [V][3][H][W], float32, device).  SSIM per
+   Wang et al. (2004): 11 x 11 Gaussian window of standard deviation 1.5, C1 = 0.01^2,
+   C2 = 0.03^2, statistics per channel plane with zero padding outside the image.
+   loss_out (device, one float) receives L when not NULL.  dL_dimage (device, same layout as
+   image) is overwritten with dL/dimage when not NULL; the L1 subgradient at image == target is 0.
+   Transient buffers (3 floats per element) come from ctx's pool.  0 <= lambda <= 1; at most
+   21845 views per call.  Errors: CS_ERR_ARG for bad sizes or NULL inputs, CS_ERR_CUDA. */
+cs_status cs_loss_l1_dssim(cs_context *ctx, const float *image, const float *target, int32_t n_views,
+                           int32_t height, int32_t width, float lambda, float *loss_out, float *dL_dimage,
+                           void *stream);
+
+/* One Adam update (Kingma and Ba 2015, Algorithm 1) of up to CS_ADAM_MAX_GROUPS parameter arrays
+   in one launch, in binary32 per element:
+     m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+     p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),  t = step >= 1.
+   Every pointer of a group is a caller-owned device float array of n elements (m and v start at
+   0 and persist between steps).  grad_abs_sum, when not NULL, receives += |g| per element (the
+   per-convex statistic of the split criterion when the group is sigma).  zero_grad != 0 sets the
+   gradient to 0 after use, ready for the next backward to accumulate into.  Groups with n = 0 are
+   skipped.  Errors: CS_ERR_ARG (NULL buffers, n < 0, step < 1, beta outside [0, 1)), CS_ERR_CUDA. */
+#define CS_ADAM_MAX_GROUPS 16
+typedef struct {
+    float *param;
+    float *grad;
+    float *m;
+    float *v;
+    float *grad_abs_sum;  /* optional */
+    int64_t n;
+    float lr;
+} cs_adam_group;
+
+typedef struct {
+    float beta1;      /* 0.9 */
+    float beta2;      /* 0.999 */
+    float eps;        /* 1e-15 */
+    int32_t zero_grad;
+} cs_adam_settings;
+
+cs_status cs_adam_step(cs_context *ctx, const cs_adam_group *groups, int32_t n_groups,
+                       const cs_adam_settings *settings, int64_t step, void *stream);
+
+/* Adaptive refinement (Sec. 3.3, supplement Sec. A): split and prune a set of raw training
+   parameters (points, log delta, log sigma, logit opacity, SH; the CS_ACT_EXP_SIGMOID convention)
+   together with their Adam moments.  Per convex, decided in binary32:
+     prune  when sigmoid(opacity) < prune_opacity, when its size (largest distance from its centre,
+            the mean of its points, to one of its points) exceeds prune_size, or when a point is
+            not finite;
+     split  otherwise when sigma_grad_abs / window_steps > split_threshold (the mean |dL/dsigma|
+            since the last refinement, as accumulated by cs_adam_step);
+     keep   otherwise.
+   Output, in input order: a kept convex once (with its moments), a split convex as K children
+   (child j: points p_j + split_scale (p_k - c), same delta and SH, sigma x split_sigma_scale,
+   opacity x split_opacity_scale, i.e. raw sigma + ln(scale) and raw opacity ln(o'/(1 - o')) with
+   the binary32 ln of the tile range; moments 0), a pruned one not at all.
+   out_* must not alias the inputs and hold `capacity` convexes.  *n_out (host) receives the
+   output count; the call synchronises the stream once to read it.  If it exceeds capacity the
+   call returns CS_ERR_BUDGET with *n_out set and writes no output (decisions are written).
+   adam_m/adam_v/out_m/out_v are all given or all NULL.  decisions (device int32 [n], 0 keep,
+   1 split, 2 prune) is optional. */
+typedef struct {
+    float *points;   /* [N][K][3] */
+    float *delta;    /* [N] */
+    float *sigma;    /* [N] */
+    float *opacity;  /* [N] */
+    float *sh;       /* [N][(D+1)^2][3] */
+} cs_param_arrays;
+
+typedef struct {
+    float split_threshold;      /* 4e-6 (supplement Sec. A) */
+    float split_scale;          /* 0.7 (indoor) or 0.6 (outdoor) */
+    float split_sigma_scale;    /* > 0; 1.5 */
+    float split_opacity_scale;  /* (0, 1]; 0.5 */
+    float prune_opacity;        /* 0.03 */
+    float prune_size;           /* 0.3 x scene size; +inf disables */
+} cs_refine_settings;
+
+cs_status cs_refine(cs_context *ctx, int64_t n, int32_t k, int32_t sh_degree, const cs_param_arrays *params,
+                    const cs_param_arrays *adam_m, const cs_param_arrays *adam_v, const float *sigma_grad_abs,
+                    int32_t window_steps, const cs_refine_settings *settings, int64_t capacity,
+                    cs_param_arrays *out_params, cs_param_arrays *out_m, cs_param_arrays *out_v, int32_t *decisions,
+                    int64_t *n_out, void *stream);
+
 /* ---- serving: continuous batching of novel-view requests (no counterpart in the paper) -------
    A server keeps several scenes resident (device buffers owned by the caller, registered with
    cs_server_add_scene) and renders view requests of mixed resolution.  A worker thread admits
@@ -246,7 +361,9 @@ typedef enum {
     CS_STAGE_BLEND = 4,           /* per-tile forward compositing */
     CS_STAGE_BLEND_BACKWARD = 5,  /* per-tile reverse compositing, per-convex gradient records */
     CS_STAGE_PREPROCESS_BACKWARD = 6, /* chain to points, delta, sigma, opacity, SH */
-    CS_STAGE_COUNT = 7
+    CS_STAGE_LOSS = 7,            /* cs_loss_l1_dssim */
+    CS_STAGE_OPTIMIZER = 8,       /* cs_adam_step */
+    CS_STAGE_COUNT = 9
 } cs_stage;
 
 /* When on, every stage of every call on this context is bracketed by CUDA events recorded on the

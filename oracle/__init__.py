@@ -51,7 +51,8 @@ class OrcCamera(ctypes.Structure):
 class OrcSettings(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float),
-                ("q_binary32", ctypes.c_int32), ("perturb_ulps", ctypes.c_float), ("line_rel", ctypes.c_float)]
+                ("q_binary32", ctypes.c_int32), ("perturb_ulps", ctypes.c_float), ("line_rel", ctypes.c_float),
+                ("tile_test", ctypes.c_int32)]
 
 
 _lib = None
@@ -78,13 +79,17 @@ def lib():
         _lib.orc_activate.restype = None
         _lib.orc_activate.argtypes = [i64, P, P, P, P, P, P]
         _lib.orc_discrete.restype = ctypes.c_int
-        _lib.orc_discrete.argtypes = [P, i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_discrete.argtypes = [P, i64, i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_tiles.restype = ctypes.c_int
+        _lib.orc_tiles.argtypes = [P, i64, i32, P, P, P, P, P, P, P]
         _lib.orc_render_pixels.restype = ctypes.c_int
         _lib.orc_render_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, u64, P, P, P, P, P, P]
         _lib.orc_backward_pixels.restype = ctypes.c_int
         _lib.orc_backward_pixels.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P, i64, P, u64, P, P, P, P, P]
         _lib.orc_alpha_support.restype = ctypes.c_int
         _lib.orc_alpha_support.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P]
+        _lib.orc_alpha_tile_mask.restype = ctypes.c_int
+        _lib.orc_alpha_tile_mask.argtypes = [P, i64, i32, P, P, P, P, i32, P, P, P]
         _lib.orc_sh_basis.restype = None
         _lib.orc_sh_basis.argtypes = [i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
         _lib.orc_num_threads.restype = ctypes.c_int
@@ -110,7 +115,7 @@ def camera(cam) -> OrcCamera:
 
 
 def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), dist_mode=0,
-             dist_power=1.0, q_binary32=False, perturb_ulps=4.0, line_rel=0.0) -> OrcSettings:
+             dist_power=1.0, q_binary32=False, perturb_ulps=4.0, line_rel=0.0, tile_test=0) -> OrcSettings:
     """Method settings plus oracle-only knobs (no counterpart in the method).
 
     q_binary32: build the hull lines from the binary32 projected points the hull was decided on
@@ -126,6 +131,7 @@ def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), di
         s.bg[i] = float(bg[i])
     s.dist_mode, s.dist_power = int(dist_mode), float(dist_power)
     s.q_binary32, s.perturb_ulps, s.line_rel = int(bool(q_binary32)), float(perturb_ulps), float(line_rel)
+    s.tile_test = int(tile_test)
     return s
 
 
@@ -201,19 +207,30 @@ def raw_gradients(scene_raw, grads: dict) -> dict:
 
 
 def discrete(scene, cam, st=None) -> dict:
-    """Discrete specification per convex: visibility, hull, tile rectangle, depth key, binary32 uv."""
+    """Discrete specification per convex: visibility, hull, tile rectangle, kept-tile count and
+    list (the exact tile test), depth key, binary32 uv.  tiles[tile_offsets[i]:][:count[i]] are
+    convex i's tiles in row-major order."""
     st = st or settings()
     a, n, k, _ = _scene_arrays(scene)
     out = dict(visible=np.zeros(n, np.int32), reason=np.zeros(n, np.int32), hull_t=np.zeros(n, np.int32),
                hull_idx=np.zeros((n, KMAX), np.int32), rect=np.zeros((n, 4), np.int32),
-               full=np.zeros(n, np.int32), depth_bits=np.zeros(n, np.uint32), uv=np.zeros((n, k, 2), np.float32))
+               full=np.zeros(n, np.int32), depth_bits=np.zeros(n, np.uint32), uv=np.zeros((n, k, 2), np.float32),
+               count=np.zeros(n, np.int32))
     c = camera(cam)
     rc = lib().orc_discrete(_p(a["points"]), n, k, _p(a["delta"]), _p(a["sigma"]), _p(a["opacity"]),
                             ctypes.byref(c), ctypes.byref(st), _p(out["visible"]), _p(out["reason"]),
                             _p(out["hull_t"]), _p(out["hull_idx"]), _p(out["rect"]), _p(out["full"]),
-                            _p(out["depth_bits"]), _p(out["uv"]))
+                            _p(out["depth_bits"]), _p(out["uv"]), _p(out["count"]))
     if rc:
         raise ValueError(f"orc_discrete failed ({rc})")
+    cnt = out["count"].astype(np.int64)
+    offsets = np.ascontiguousarray(np.cumsum(cnt) - cnt)
+    tiles = np.zeros(int(cnt.sum()), np.int32)
+    rc = lib().orc_tiles(_p(a["points"]), n, k, _p(a["delta"]), _p(a["sigma"]), _p(a["opacity"]), ctypes.byref(c),
+                         ctypes.byref(st), _p(offsets), _p(tiles))
+    if rc:
+        raise ValueError(f"orc_tiles failed ({rc})")
+    out["tiles"], out["tile_offsets"] = tiles, offsets
     return out
 
 
@@ -298,6 +315,20 @@ def alpha_support(scene, cam, st=None) -> np.ndarray:
     return bbox
 
 
+def alpha_tile_mask(scene, cam, st=None) -> np.ndarray:
+    """[n][tiles] mask: 1 where some pixel of the tile has binary64 alpha >= tau."""
+    st = st or settings()
+    a, n, k, deg = _scene_arrays(scene)
+    nt = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    out = np.zeros((n, nt), np.uint8)
+    c = camera(cam)
+    rc = lib().orc_alpha_tile_mask(_p(a["points"]), n, k, _p(a["delta"]), _p(a["sigma"]), _p(a["opacity"]),
+                                   _p(a["sh"]), deg, ctypes.byref(c), ctypes.byref(st), _p(out))
+    if rc:
+        raise ValueError(f"orc_alpha_tile_mask failed ({rc})")
+    return out
+
+
 def sh_basis(deg: int, d) -> tuple:
     Y = np.zeros(16)
     dY = np.zeros((16, 3))
@@ -312,13 +343,11 @@ def tile_lists(disc: dict, cam) -> dict:
     """
     vis = np.nonzero(disc["visible"])[0]
     order = vis[np.lexsort((vis, disc["depth_bits"][vis]))]
-    ntx = (cam.width + 15) // 16
     lists = {}
     for cid in order:
-        x0, y0, x1, y1 = disc["rect"][cid]
-        for ty in range(y0, y1 + 1):
-            for tx in range(x0, x1 + 1):
-                lists.setdefault(ty * ntx + tx, []).append(int(cid))
+        o, c = disc["tile_offsets"][cid], disc["count"][cid]
+        for t in disc["tiles"][o:o + c]:
+            lists.setdefault(int(t), []).append(int(cid))
     return {t: np.asarray(v, np.int64) for t, v in lists.items()}
 
 
@@ -328,19 +357,14 @@ def num_threads() -> int:
 
 def sorted_pairs(disc: dict, cam, tile_base: int = 0, rec_base: int = 0):
     """Expected sorted (tile, record) pairs of one view: visible convexes in (depth bits, id) order
-    each list the tiles of their range in row-major order, then a stable sort by tile index.
+    each list their kept tiles in row-major order, then a stable sort by tile index.
     Returns (keys = tile_base + tile index, values = rec_base + convex id)."""
     vis = np.nonzero(disc["visible"])[0]
     order = vis[np.lexsort((vis, disc["depth_bits"][vis]))]
-    r = disc["rect"][order].astype(np.int64)
-    nx = r[:, 2] - r[:, 0] + 1
-    ny = r[:, 3] - r[:, 1] + 1
-    cnt = nx * ny
+    cnt = disc["count"][order].astype(np.int64)
     rep = np.repeat(np.arange(len(order)), cnt)
     within = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
-    tx = r[rep, 0] + within % nx[rep]
-    ty = r[rep, 1] + within // nx[rep]
-    keys = ty * ((cam.width + 15) // 16) + tx
+    keys = disc["tiles"][disc["tile_offsets"][order][rep] + within].astype(np.int64)
     vals = order[rep]
     perm = np.argsort(keys, kind="stable")
     return (keys[perm] + tile_base).astype(np.int64), (vals[perm] + rec_base).astype(np.int64)

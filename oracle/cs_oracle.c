@@ -75,6 +75,7 @@ typedef struct {
        a = first hull vertex (the size of binary32 line evaluation relative to an anchor vertex);
        otherwise the vertex-motion model (every hull vertex moves by perturb_ulps ulps) is used. */
     float line_rel;
+    int32_t tile_test; /* the method's exact tile test (cs_settings.tile_test) */
 } orc_settings;
 
 /* flags reported per pixel by the continuous render */
@@ -289,6 +290,43 @@ void orc_activate(int64_t n, const float *raw_delta, const float *raw_sigma, con
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Exact tile test.  The rectangle bounds the mitre-offset hull {q : max_t L_t(q) <= r}, which  */
+/* holds every pixel where o I >= tau; a tile of the rectangle is kept unless one hull line's  */
+/* smallest value over the tile's pixel centres (a corner of [16 tx + 0.5, 16 tx + 15.5] x      */
+/* [16 ty + 0.5, 16 ty + 15.5], chosen by the signs of the normal) exceeds r, so it separates  */
+/* the tile from that set (a separating-axis test along the hull normals; the tile's own axes   */
+/* are the rectangle).  It is evaluated on the lines as the screen record stores them,          */
+/* A = kappa n_x, B = kappa n_y, C = kappa n.(anchor - v_t), kappa = d^p delta log2(e), against */
+/* rk = kappa r, with a margin of 2^-20 times the magnitudes involved for binary32 rounding.   */
+/* Rectangles of fewer than ORC_SAT_MIN_TILES or more than ORC_SAT_MAX_TILES tiles, and        */
+/* whole-screen ones, are kept whole.                                                          */
+/* ------------------------------------------------------------------------------------------ */
+#define ORC_SAT_MIN_TILES 3
+#define ORC_SAT_MAX_TILES 1024
+
+static int tile_kept(const float *A, const float *B, const float *C, int T, float ax, float ay, float rk, int tx,
+                     int ty) {
+    float fx = (float)(16 * tx), fy = (float)(16 * ty);
+    float X0 = fx + 0.5f, X1 = fx + 15.5f, Y0 = fy + 0.5f, Y1 = fy + 15.5f;
+    for (int t = 0; t < T; t++) {
+        float X = A[t] >= 0.0f ? X0 : X1;
+        float Y = B[t] >= 0.0f ? Y0 : Y1;
+        float dx = X - ax;
+        float dy = Y - ay;
+        float pa = A[t] * dx;
+        float pb = B[t] * dy;
+        float L = pa + pb;
+        L = L + C[t];
+        float mag = fabsf(pa) + fabsf(pb);
+        mag = mag + fabsf(C[t]);
+        float margin = mag * 0x1p-20f;
+        float bound = rk + margin;
+        if (L > bound) return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Discrete specification of one convex (binary32).                                           */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -300,11 +338,15 @@ typedef struct {
     float uv[ORC_KMAX][2];
     uint32_t depth_bits;
     int tx0, ty0, tx1, ty1;
+    int count; /* tiles kept by the exact tile test (the whole rectangle when not tested) */
+    int tested;
+    float lA[ORC_KMAX], lB[ORC_KMAX], lC[ORC_KMAX]; /* hull lines in record form (see below) */
+    float ax, ay, rk;
 } orc_disc;
 
 enum {
     R_OK = 0, R_NONFINITE = 1, R_NONPOSITIVE = 2, R_NEAR = 3, R_RANGE = 4, R_DIST = 5,
-    R_OPACITY = 6, R_HULL = 7, R_EDGE = 8, R_OFFSCREEN = 9, R_POWER = 10
+    R_OPACITY = 6, R_HULL = 7, R_EDGE = 8, R_OFFSCREEN = 9, R_POWER = 10, R_NO_TILE = 11
 };
 
 #define ORC_COORD_LIMIT 1048576.0f /* 2^20 px */
@@ -456,13 +498,43 @@ static void discrete_convex(const float *P, int K, float delta, float sigma, flo
     if (tx0 > tx1 || ty0 > ty1 || ntx <= 0 || nty <= 0) { out->reason = R_OFFSCREEN; return; }
     out->full = full;
     out->tx0 = tx0; out->ty0 = ty0; out->tx1 = tx1; out->ty1 = ty1;
+    /* 8. the record's lines: kappa = d^p delta log2 e; A, B, C relative to the anchor vertex */
+    float kappa = dp * 0x1.715476p+0f;
+    const float *a0 = out->uv[out->idx[0]];
+    out->ax = a0[0];
+    out->ay = a0[1];
+    for (int t = 0; t < T; t++) {
+        const float *v = out->uv[out->idx[t]];
+        out->lA[t] = kappa * nx[t];
+        out->lB[t] = kappa * ny[t];
+        float du = a0[0] - v[0];
+        float dv = a0[1] - v[1];
+        float cu = nx[t] * du;
+        float cv = ny[t] * dv;
+        float cs = cu + cv;
+        out->lC[t] = kappa * cs;
+    }
+    out->rk = rp * kappa;
+    /* 9. tiles kept by the exact test */
+    int64_t area = (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    out->tested = st->tile_test && !full && area >= ORC_SAT_MIN_TILES && area <= ORC_SAT_MAX_TILES;
+    if (out->tested) {
+        int cnt = 0;
+        for (int ty = ty0; ty <= ty1; ty++)
+            for (int tx = tx0; tx <= tx1; tx++)
+                cnt += tile_kept(out->lA, out->lB, out->lC, T, out->ax, out->ay, out->rk, tx, ty);
+        out->count = cnt;
+    } else {
+        out->count = (int)area;
+    }
+    if (out->count == 0) { out->reason = R_NO_TILE; return; }
     out->visible = 1;
 }
 
 int orc_discrete(const float *points, int64_t n, int32_t k, const float *delta, const float *sigma,
                  const float *opacity, const orc_camera *cam, const orc_settings *st,
                  int32_t *visible, int32_t *reason, int32_t *hull_t, int32_t *hull_idx, int32_t *rect,
-                 int32_t *full, uint32_t *depth_bits, float *uv) {
+                 int32_t *full, uint32_t *depth_bits, float *uv, int32_t *count) {
     if (k < 3 || k > ORC_KMAX || n < 0) return -1;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; i++) {
@@ -479,6 +551,28 @@ int orc_discrete(const float *points, int64_t n, int32_t k, const float *delta, 
         if (full) full[i] = d.full;
         if (depth_bits) depth_bits[i] = d.depth_bits;
         if (uv) for (int j = 0; j < 2 * k; j++) uv[2 * k * i + j] = d.uv[j / 2][j % 2];
+        if (count) count[i] = d.visible ? d.count : 0;
+    }
+    return 0;
+}
+
+/* The kept tiles (ty * tiles_x + tx, row-major within the rectangle) of every drawn convex,
+   written at tiles[offsets[i] ...]; offsets come from the counts of orc_discrete. */
+int orc_tiles(const float *points, int64_t n, int32_t k, const float *delta, const float *sigma,
+              const float *opacity, const orc_camera *cam, const orc_settings *st, const int64_t *offsets,
+              int32_t *tiles) {
+    if (k < 3 || k > ORC_KMAX || n < 0) return -1;
+    const int ntx = tiles_x(cam);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; i++) {
+        orc_disc d;
+        discrete_convex(points + 3 * k * i, k, delta[i], sigma[i], opacity[i], cam, st, &d);
+        if (!d.visible) continue;
+        int64_t o = offsets[i];
+        for (int ty = d.ty0; ty <= d.ty1; ty++)
+            for (int tx = d.tx0; tx <= d.tx1; tx++)
+                if (!d.tested || tile_kept(d.lA, d.lB, d.lC, d.T, d.ax, d.ay, d.rk, tx, ty))
+                    tiles[o++] = ty * ntx + tx;
     }
     return 0;
 }
@@ -859,6 +953,33 @@ int orc_alpha_support(const float *points, int64_t n, int32_t k, const float *de
                 }
         }
         bbox[4 * i] = x0; bbox[4 * i + 1] = y0; bbox[4 * i + 2] = x1; bbox[4 * i + 3] = y1;
+    }
+    release(&pr);
+    return 0;
+}
+
+/* per convex and tile, 1 if some pixel of the tile has binary64 alpha >= tau (mask [n][tiles]) */
+int orc_alpha_tile_mask(const float *points, int64_t n, int32_t k, const float *delta, const float *sigma,
+                        const float *opacity, const float *sh, int32_t sh_deg, const orc_camera *cam,
+                        const orc_settings *st, uint8_t *mask) {
+    orc_prepared pr;
+    int rc = prepare(&pr, points, n, k, delta, sigma, opacity, sh, sh_deg, cam, st, 0);
+    if (rc) { release(&pr); return rc; }
+    const int ntx = tiles_x(cam), nt = ntx * tiles_y(cam);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; i++) {
+        uint8_t *m = mask + (size_t)i * nt;
+        memset(m, 0, (size_t)nt);
+        if (!pr.dsc[i].visible) continue;
+        for (int y = 0; y < cam->height; y++)
+            for (int x = 0; x < cam->width; x++) {
+                double L[ORC_KMAX], phi, I;
+                if (!indicator(&pr.cv[i], st, 0, i, x + 0.5, y + 0.5, L, &phi, &I)) continue;
+                double a = pr.cv[i].o * I;
+                if (a > (double)st->alpha_max) a = st->alpha_max;
+                if (a < (double)st->tau) continue;
+                m[(y / 16) * ntx + x / 16] = 1;
+            }
     }
     release(&pr);
     return 0;

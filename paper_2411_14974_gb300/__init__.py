@@ -5,6 +5,7 @@ projected (Eq. 4), their 2D hull becomes lines, delta/sigma are scaled by the ca
 (Eq. S1/S2), and pixels composite the smooth indicators front to back (Eq. 5).  The compute runs
 in the CUDA library behind include/convex_splat.h; this package only marshals arguments.
 """
-from .rasterizer import (ARRAYS, WORK_FIELDS, Context, SceneTensors, Server, Settings, State, backward,  # noqa: F401
-                         camera_struct, forward, launch_count, profile_enable, profile_read, render, step_host,
+from .rasterizer import (ARRAYS, PARAMS, WORK_FIELDS, Context, RefineSettings, SceneTensors, Server,  # noqa: F401
+                         Settings, State, TrainConfig, Trainer, adam_step, backward, camera_struct, forward,
+                         launch_count, loss_l1_dssim, profile_enable, profile_read, refine, render, step_host,
                          work_counts)

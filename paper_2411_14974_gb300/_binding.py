@@ -15,13 +15,36 @@ class CsCamera(ctypes.Structure):
 
 class CsSettings(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float)]
+                ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float),
+                ("tile_test", ctypes.c_int32)]
 
 
 class CsScene(ctypes.Structure):
     _fields_ = [("points", ctypes.c_void_p), ("delta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
                 ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("n", ctypes.c_int64),
-                ("k", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("activation", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
+
+
+class CsAdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("grad_abs_sum", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float)]
+
+
+class CsAdamSettings(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("zero_grad", ctypes.c_int32)]
+
+
+class CsParamArrays(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("delta", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class CsRefineSettings(ctypes.Structure):
+    _fields_ = [("split_threshold", ctypes.c_float), ("split_scale", ctypes.c_float),
+                ("split_sigma_scale", ctypes.c_float), ("split_opacity_scale", ctypes.c_float),
+                ("prune_opacity", ctypes.c_float), ("prune_size", ctypes.c_float)]
 
 
 class CsCompletion(ctypes.Structure):
@@ -51,6 +74,15 @@ _PROTOTYPES = {
     "cs_work_counts": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "cs_forward_static": (ctypes.c_int, [ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera),
                                          ctypes.POINTER(CsSettings), _P, _P, _P]),
+    "cs_loss_l1_dssim": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                        _P, _P, _P]),
+    "cs_adam_step": (ctypes.c_int, [_P, ctypes.POINTER(CsAdamGroup), ctypes.c_int32, ctypes.POINTER(CsAdamSettings),
+                                    ctypes.c_int64, _P]),
+    "cs_refine": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(CsParamArrays),
+                                 ctypes.POINTER(CsParamArrays), ctypes.POINTER(CsParamArrays), _P, ctypes.c_int32,
+                                 ctypes.POINTER(CsRefineSettings), ctypes.c_int64, ctypes.POINTER(CsParamArrays),
+                                 ctypes.POINTER(CsParamArrays), ctypes.POINTER(CsParamArrays), _P,
+                                 ctypes.POINTER(ctypes.c_int64), _P]),
     "cs_server_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32,
                                         ctypes.POINTER(CsSettings), ctypes.POINTER(_P)]),
     "cs_server_destroy": (None, [_P]),
@@ -63,7 +95,9 @@ _PROTOTYPES = {
     "cs_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
 }
 
-STAGES = ("preprocess", "depth_sort", "scan_emit", "tile_sort", "blend", "blend_backward", "preprocess_backward")
+STAGES = ("preprocess", "depth_sort", "scan_emit", "tile_sort", "blend", "blend_backward", "preprocess_backward",
+          "loss", "optimizer")
+ADAM_MAX_GROUPS = 16
 
 _lib = None
 

@@ -111,6 +111,7 @@ extern "C" void cs_default_settings(cs_settings *s) {
     s->bg[0] = s->bg[1] = s->bg[2] = 0.f;
     s->dist_mode = 0;
     s->dist_power = 1.0f;
+    s->tile_test = 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -199,6 +200,7 @@ cs_status cs::check_settings(const cs_settings *st) {
     if (!(st->alpha_max > 0.f && st->alpha_max <= 1.f)) return fail(CS_ERR_ARG, "alpha_max must be in (0, 1]");
     if (!(st->t_min >= 0.f && st->t_min < 1.f)) return fail(CS_ERR_ARG, "t_min must be in [0, 1)");
     if (st->dist_mode != 0 && st->dist_mode != 1) return fail(CS_ERR_ARG, "dist_mode must be 0 or 1");
+    if (st->tile_test != 0 && st->tile_test != 1) return fail(CS_ERR_ARG, "tile_test must be 0 or 1");
     const float p = st->dist_power;
     if (!(p == 0.f || p == 0.5f || p == 1.f || p == 2.f)) return fail(CS_ERR_ARG, "dist_power must be 0, 0.5, 1 or 2");
     for (int i = 0; i < 3; ++i)
@@ -225,6 +227,10 @@ cs_status cs::check_scene(const cs_scene *s) {
     if (s->n < 0 || s->n > (int64_t)1 << 31) return fail(CS_ERR_ARG, "scene size %lld out of range", (long long)s->n);
     if (s->k < 3 || s->k > KMAX) return fail(CS_ERR_ARG, "k = %d: 3 <= k <= 8 points per convex", s->k);
     if (s->sh_degree < 0 || s->sh_degree > 3) return fail(CS_ERR_ARG, "sh_degree must be 0..3");
+    if (s->activation != CS_ACT_NONE && s->activation != CS_ACT_EXP_SIGMOID)
+        return fail(CS_ERR_ARG, "activation must be CS_ACT_NONE or CS_ACT_EXP_SIGMOID");
+    if (s->storage != CS_STORE_F32 && s->storage != CS_STORE_F16 && s->storage != CS_STORE_BF16)
+        return fail(CS_ERR_ARG, "storage must be CS_STORE_F32, CS_STORE_F16 or CS_STORE_BF16");
     if (s->n > 0 && (!s->points || !s->delta || !s->sigma || !s->opacity || !s->sh))
         return fail(CS_ERR_ARG, "scene has a NULL buffer");
     return CS_OK;
@@ -248,6 +254,7 @@ Settings cs::to_settings(const cs_settings &s) {
     o.tau = s.tau; o.alpha_max = s.alpha_max; o.t_min = s.t_min;
     o.bg[0] = s.bg[0]; o.bg[1] = s.bg[1]; o.bg[2] = s.bg[2];
     o.dist_mode = s.dist_mode; o.dist_power = s.dist_power;
+    o.tile_test = s.tile_test;
     return o;
 }
 
@@ -312,6 +319,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     uint32_t *sort_keys_a = nullptr, *sort_keys_b = nullptr, *sort_vals_a = nullptr, *sort_vals_b = nullptr;
     uint32_t *offsets = nullptr, *radix_tmp = nullptr, *pk_b = nullptr, *pv_b = nullptr;
     unsigned long long *scan_tmp = nullptr, *total = nullptr;
+    float *radii = nullptr;
     uint64_t P = 0;
     bool in_b = false;
     uint32_t max_view_tiles = 1;
@@ -330,6 +338,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     CS_TRY(pool_alloc(ctx, (void **)&s->rects, (size_t)R * 8, stream), "alloc rects");
     CS_TRY(pool_alloc(ctx, (void **)&s->counts, (size_t)R * 4, stream), "alloc counts");
     CS_TRY(pool_alloc(ctx, (void **)&s->bboxes, (size_t)R * 16, stream), "alloc boxes");
+    CS_TRY(pool_alloc(ctx, (void **)&radii, (size_t)R * 4, stream), "alloc radii");
     CS_TRY(pool_alloc(ctx, (void **)&s->ranges, (size_t)tiles * 8, stream), "alloc ranges");
     CS_TRY(pool_alloc(ctx, (void **)&s->n_last, pix_total * 4, stream), "alloc n_last");
     {
@@ -351,7 +360,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
            "copy views");
     {
         StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
-        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes};
+        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes, radii};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
     }
     // depth order of the records
@@ -401,9 +410,11 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
-        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, R, local_bits, s->pair_keys,
-                                 s->pair_vals, stream),
+        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii, R,
+                                 local_bits, s->pair_keys, s->pair_vals, stream),
                "emit pairs");
+        pool_free(radii, stream);
+        radii = nullptr;
     }
     // stable sort of the pairs by tile
     {
@@ -439,6 +450,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         }
     }
 cleanup:
+    pool_free(radii, stream);
     pool_free(sort_keys_a, stream);
     pool_free(sort_keys_b, stream);
     pool_free(sort_vals_a, stream);
@@ -451,15 +463,6 @@ cleanup:
     pool_free(pv_b, stream);
     return st_code;
 }
-
-struct DeviceGuard {
-    int prev = 0;
-    explicit DeviceGuard(int d) {
-        cudaGetDevice(&prev);
-        cudaSetDevice(d);
-    }
-    ~DeviceGuard() { cudaSetDevice(prev); }
-};
 
 extern "C" cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs_camera *cams, int32_t n_views,
                                 const cs_settings *settings, float *image, float *t_final, cs_fwd_state **state_out,
@@ -492,7 +495,7 @@ extern "C" cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs
         fill_view(vd, cams[v]);
         vd.points = scene->points; vd.delta = scene->delta; vd.sigma = scene->sigma;
         vd.opacity = scene->opacity; vd.sh = scene->sh;
-        vd.n = scene->n; vd.k = scene->k; vd.sh_degree = scene->sh_degree;
+        vd.n = scene->n; vd.k = scene->k; vd.sh_degree = scene->sh_degree; vd.activation = scene->activation; vd.storage = scene->storage;
         vd.image = image + (size_t)v * 3 * hw;
         vd.t_final = t_final ? t_final + (size_t)v * hw : nullptr;
     }
@@ -531,8 +534,8 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_PREPROCESS_BACKWARD, stream);
             PreprocessGrads g{dpoints, ddelta, dsigma, dopacity, dsh};
-            e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->scene.sh_degree, s->st, s->records,
-                                           s->counts, grads, g, V > 1, stream);
+            e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->scene.sh_degree, s->scene.storage,
+                                           s->st, s->records, s->counts, grads, g, V > 1, stream);
         }
         if (e != cudaSuccess) st_code = fail_cuda(e, "backward");
     }
@@ -610,10 +613,12 @@ extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_
     cudaStream_t stream = (cudaStream_t)stream_ptr;
     const int64_t n = sh->n;
     const int nb = (sh->sh_degree + 1) * (sh->sh_degree + 1);
-    const size_t b_pts = (size_t)n * sh->k * 3 * 4, b_one = (size_t)n * 4, b_sh = (size_t)n * nb * 3 * 4;
+    const size_t esz = sh->storage == CS_STORE_F32 ? 4 : 2;  // parameters as stored; gradients float32
+    const size_t b_pts = (size_t)n * sh->k * 3, b_one = (size_t)n, b_sh = (size_t)n * nb * 3;
     const size_t b_img = (size_t)n_views * 3 * cams[0].width * cams[0].height * 4;
     float *d[12] = {};
-    const size_t sizes[12] = {b_pts, b_one, b_one, b_one, b_sh, b_img, b_img, b_pts, b_one, b_one, b_one, b_sh};
+    const size_t sizes[12] = {b_pts * esz, b_one * esz, b_one * esz, b_one * esz, b_sh * esz, b_img,
+                              b_img,       b_pts * 4,   b_one * 4,   b_one * 4,   b_one * 4, b_sh * 4};
     const bool bwd = dL_host != nullptr;
     const int nbuf = bwd ? 12 : 6;
     cs_fwd_state *state = nullptr;

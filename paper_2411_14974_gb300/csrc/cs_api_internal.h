@@ -61,6 +61,16 @@ Settings to_settings(const cs_settings &s);
 cs_status run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream);
 void state_free(cs_fwd_state *s);
 
+// makes ctx's device current for the lifetime of the guard
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        cudaSetDevice(d);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
 // brackets a stage with events when the context is profiling
 class StageTimer {
   public:

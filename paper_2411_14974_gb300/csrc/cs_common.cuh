@@ -38,9 +38,11 @@ struct ViewDesc {
     uint32_t tile_base;  // first global tile index of this view
     int64_t rec_base;    // first record index of this view
     // scene (device)
-    const float *points, *delta, *sigma, *opacity, *sh;
+    const void *points, *delta, *sigma, *opacity, *sh;  // elements of type `storage`
     int64_t n;
     int32_t k, sh_degree;
+    int32_t activation;  // 0: delta, sigma, opacity as given; 1: exp, exp, sigmoid of the given values
+    int32_t storage;     // cs_storage: float32, binary16 or bfloat16 parameters
     // outputs (device)
     float *image;     // [3][H][W]
     float *t_final;   // [H][W]
@@ -52,6 +54,7 @@ struct Settings {
     float bg[3];
     int32_t dist_mode;
     float dist_power;
+    int32_t tile_test;
 };
 
 __host__ __device__ inline uint32_t hull_pack_count(uint32_t packed) { return packed & 15u; }
@@ -64,6 +67,7 @@ struct PreprocessOut {
     uint2 *rects;          // [R]
     uint32_t *counts;      // [R]
     float4 *bboxes;        // [R] pixel box (xmin, ymin, xmax, ymax) holding every pixel with alpha >= tau
+    float *radii;          // [R] kappa r, the tile test's bound in record units
 };
 cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n,
                               int k, const Settings &st, const PreprocessOut &out, cudaStream_t s);
@@ -72,7 +76,7 @@ struct PreprocessGrads {
     float *dpoints, *ddelta, *dsigma, *dopacity, *dsh;
 };
 cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k, int sh_degree,
-                                       const Settings &st, const float4 *records, const uint32_t *counts,
+                                       int storage, const Settings &st, const float4 *records, const uint32_t *counts,
                                        const float4 *grad_records, const PreprocessGrads &g, bool atomic,
                                        cudaStream_t s);
 
@@ -95,8 +99,9 @@ cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint3
                              uint32_t *keys, cudaStream_t s);
 // pair key = view << local_bits | tile index within the view
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
-                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
-                              int local_bits, uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
+                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
+                              const float4 *records, const float *radii, int64_t n_records, int local_bits,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
                                uint2 *ranges, int64_t n_tiles, cudaStream_t s);
 

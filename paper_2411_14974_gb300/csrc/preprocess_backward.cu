@@ -1,0 +1,299 @@
+// Per-(view, convex) backward preprocess of the convex tile rasterizer: one thread per drawn
+// convex applies the chain rule from the per-record gradient accumulated by the blend backward
+// (lines, sigma', opacity, colour) to the hull vertices, the projected points, the 3D points
+// (Eq. 4 Jacobian), delta, sigma, the camera distance (Eq. S1/S2), the opacity and the SH
+// coefficients, and, for training parameters, through the exp / sigmoid activations (Sec. 3.3).
+#include "projection.cuh"
+
+namespace cs {
+namespace {
+
+// Backward: one thread per drawn convex.  With one view, the points and SH gradients of the
+// block's convexes are accumulated (+=) in shared memory and read / written back with coalesced
+// accesses; with several views, convexes are shared between views and use global atomics.
+template <int K, int DEG, bool ATOMIC, int STG>
+__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const ViewDesc *__restrict__ views, Settings st,
+                                                                     const float4 *__restrict__ records,
+                                                                     const uint32_t *__restrict__ counts,
+                                                                     const float4 *__restrict__ grads,
+                                                                     PreprocessGrads out) {
+    constexpr int NB = (DEG + 1) * (DEG + 1);
+    constexpr int PW = K * 3, SW = NB * 3;           // words per convex
+    constexpr int PS = PW | 1, SS = SW | 1;          // odd strides: no bank conflicts
+    __shared__ float s_dp[ATOMIC ? 1 : PRE_THREADS * PS];
+    __shared__ float s_dsh[ATOMIC ? 1 : PRE_THREADS * SS];
+    const ViewDesc &vd = views[blockIdx.y];
+    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
+    if (i0 >= vd.n) return;
+    const int cnt = (int)min((int64_t)PRE_THREADS, vd.n - i0);
+    if (!ATOMIC) {
+        if (out.dpoints)
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) s_dp[(q / PW) * PS + q % PW] = out.dpoints[i0 * PW + q];
+        if (out.dsh)
+            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) s_dsh[(q / SW) * SS + q % SW] = out.dsh[i0 * SW + q];
+        __syncthreads();
+    }
+    const int64_t i = i0 + threadIdx.x;
+    const int64_t rec = vd.rec_base + i;
+    if (i < vd.n && counts[rec] != 0) {
+        float gw[GRAD_WORDS];
+        const float4 h0 = records[rec * (REC_WORDS / 4)], h1 = records[rec * (REC_WORDS / 4) + 1];
+#pragma unroll
+        for (int q = 0; q < GRAD_WORDS / 4; ++q) {
+            const float4 b = grads[rec * (GRAD_WORDS / 4) + q];
+            gw[4 * q] = b.x; gw[4 * q + 1] = b.y; gw[4 * q + 2] = b.z; gw[4 * q + 3] = b.w;
+        }
+        (void)h0;
+        const uint32_t hull = __float_as_uint(h1.w);
+        const int T = (int)hull_pack_count(hull);
+        float delta = ld_param<STG>(vd.delta, i), sigma = ld_param<STG>(vd.sigma, i);
+        if (vd.activation) {
+            delta = exp_act(delta);
+            sigma = exp_act(sigma);
+        }
+        float p[K][3], xc[K][3], u[K], v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            p[k][0] = ld_param<STG>(vd.points, i * PW + 3 * k);
+            p[k][1] = ld_param<STG>(vd.points, i * PW + 3 * k + 1);
+            p[k][2] = ld_param<STG>(vd.points, i * PW + 3 * k + 2);
+            const float3 x = xform(vd, p[k][0], p[k][1], p[k][2]);
+            xc[k][0] = x.x; xc[k][1] = x.y; xc[k][2] = x.z;
+            u[k] = __fadd_rn(__fmul_rn(vd.fx, __fdiv_rn(x.x, x.z)), vd.cx);
+            v[k] = __fadd_rn(__fmul_rn(vd.fy, __fdiv_rn(x.y, x.z)), vd.cy);
+        }
+        float c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sum = p[0][a];
+#pragma unroll
+            for (int k = 1; k < K; ++k) sum = __fadd_rn(sum, p[k][a]);
+            c[a] = __fdiv_rn(sum, (float)K);
+        }
+        const float3 cc = xform(vd, c[0], c[1], c[2]);
+        const float depth = sqrtf(cc.x * cc.x + cc.y * cc.y + cc.z * cc.z);
+        const float ds = st.dist_mode == 1 ? cc.z : depth;
+        const float g = scale_power(ds, st.dist_power);
+        const float kappa = g * delta * LOG2E;
+
+        // lines -> hull vertices -> projected points
+        float hu[KMAX], hv[KMAX];
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t)
+            if (t < T) select_point<K>(u, v, hull_pack_index(hull, t), hu[t], hv[t]);
+        const float ax = hu[0], ay = hv[0];
+        float dkappa = 0.f;
+        float dhu[KMAX], dhv[KMAX];
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) dhu[t] = dhv[t] = 0.f;
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            if (t >= T) break;
+            const int t1 = (t + 1 == T) ? 0 : t + 1;
+            float wx = hu[0], wy = hv[0];
+#pragma unroll
+            for (int q = 1; q < KMAX; ++q)
+                if (q == t1) { wx = hu[q]; wy = hv[q]; }
+            const float ex = wx - hu[t], ey = wy - hv[t];
+            const float len = sqrtf(ex * ex + ey * ey);
+            const float il = 1.0f / len;
+            const float nx = ey * il, ny = -ex * il;
+            const float gA = gw[3 * t], gB = gw[3 * t + 1], gC = gw[3 * t + 2];
+            const float rx = ax - hu[t], ry = ay - hv[t];
+            dkappa += gA * nx + gB * ny + gC * (nx * rx + ny * ry);
+            const float dnx = kappa * (gA + gC * rx), dny = kappa * (gB + gC * ry);
+            dhu[t] -= kappa * gC * nx;
+            dhv[t] -= kappa * gC * ny;
+            const float nd = nx * dnx + ny * dny;
+            const float dux = (dnx - nx * nd) * il, duy = (dny - ny * nd) * il;
+            const float dex = -duy, dey = dux;  // n = (ey, -ex)/|e|
+#pragma unroll
+            for (int q = 0; q < KMAX; ++q)
+                if (q == t1) { dhu[q] += dex; dhv[q] += dey; }
+            dhu[t] -= dex;
+            dhv[t] -= dey;
+        }
+        float du[K], dv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) du[k] = dv[k] = 0.f;
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+            if (t >= T) break;
+            const int k = hull_pack_index(hull, t);
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (q == k) { du[q] += dhu[t]; dv[q] += dhv[t]; }
+        }
+        // delta, sigma, opacity, distance
+        const float gsig = gw[G_SIG];
+        float dd_delta = dkappa * g * LOG2E, dd_sigma = gsig * g, dd_opa = gw[G_OPA];
+        if (vd.activation) {  // to the raw values: d exp = exp, d sigmoid = o (1 - o)
+            const float o = sigmoid_act(ld_param<STG>(vd.opacity, i));
+            dd_delta *= delta;
+            dd_sigma *= sigma;
+            dd_opa *= o * (1.0f - o);
+        }
+        if (ATOMIC) {
+            if (out.ddelta && dd_delta != 0.f) atomicAdd(out.ddelta + i, dd_delta);
+            if (out.dsigma && dd_sigma != 0.f) atomicAdd(out.dsigma + i, dd_sigma);
+            if (out.dopacity && dd_opa != 0.f) atomicAdd(out.dopacity + i, dd_opa);
+        } else {
+            if (out.ddelta) out.ddelta[i] += dd_delta;
+            if (out.dsigma) out.dsigma[i] += dd_sigma;
+            if (out.dopacity) out.dopacity[i] += dd_opa;
+        }
+        const float dg = dkappa * delta * LOG2E + gsig * sigma;
+        float dds;
+        if (st.dist_power == 1.0f) dds = dg;
+        else if (st.dist_power == 0.0f) dds = 0.f;
+        else if (st.dist_power == 0.5f) dds = dg * 0.5f / sqrtf(ds);
+        else dds = dg * 2.f * ds;
+        float dcc[3] = {0.f, 0.f, 0.f};
+        if (st.dist_mode == 1) dcc[2] = dds;
+        else { dcc[0] = dds * cc.x / depth; dcc[1] = dds * cc.y / depth; dcc[2] = dds * cc.z / depth; }
+        float dc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dc[a] = vd.R[a] * dcc[0] + vd.R[3 + a] * dcc[1] + vd.R[6 + a] * dcc[2];
+        // colour: dsh and the gradient of the view direction (basis streamed term by term)
+        {
+            const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
+            const float iwl = rsqrtf(wx * wx + wy * wy + wz * wz);
+            const float dx = wx * iwl, dy = wy * iwl, dz = wz * iwl;
+            const int64_t shb = i * SW;
+            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                float gx, gy, gz;
+                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                raw0 += ld_param<STG>(vd.sh, shb + 3 * j) * Yj;
+                raw1 += ld_param<STG>(vd.sh, shb + 3 * j + 1) * Yj;
+                raw2 += ld_param<STG>(vd.sh, shb + 3 * j + 2) * Yj;
+            }
+            const float gr0 = raw0 > 0.f ? gw[G_RGB] : 0.f;
+            const float gr1 = raw1 > 0.f ? gw[G_RGB + 1] : 0.f;
+            const float gr2 = raw2 > 0.f ? gw[G_RGB + 2] : 0.f;
+            float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+            if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    float gx, gy, gz;
+                    const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                    const float d0 = Yj * gr0, d1 = Yj * gr1, d2 = Yj * gr2;
+                    if (ATOMIC) {
+                        if (out.dsh) {
+                            if (d0 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j, d0);
+                            if (d1 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 1, d1);
+                            if (d2 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 2, d2);
+                        }
+                    } else {
+                        s_dsh[threadIdx.x * SS + 3 * j] += d0;
+                        s_dsh[threadIdx.x * SS + 3 * j + 1] += d1;
+                        s_dsh[threadIdx.x * SS + 3 * j + 2] += d2;
+                    }
+                    if (DEG > 0) {
+                        const float sg = ld_param<STG>(vd.sh, shb + 3 * j) * gr0 +
+                                         ld_param<STG>(vd.sh, shb + 3 * j + 1) * gr1 +
+                                         ld_param<STG>(vd.sh, shb + 3 * j + 2) * gr2;
+                        ddx += sg * gx;
+                        ddy += sg * gy;
+                        ddz += sg * gz;
+                    }
+                }
+            }
+            const float dd = dx * ddx + dy * ddy + dz * ddz;
+            dc[0] += (ddx - dx * dd) * iwl;
+            dc[1] += (ddy - dy * dd) * iwl;
+            dc[2] += (ddz - dz * dd) * iwl;
+        }
+        const float invK = 1.0f / (float)K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float iz = 1.0f / xc[k][2];
+            const float dx = du[k] * vd.fx * iz, dy = dv[k] * vd.fy * iz;
+            const float dz = -(du[k] * vd.fx * xc[k][0] + dv[k] * vd.fy * xc[k][1]) * iz * iz;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float d = vd.R[a] * dx + vd.R[3 + a] * dy + vd.R[6 + a] * dz + dc[a] * invK;
+                if (ATOMIC) {
+                    if (out.dpoints && d != 0.f) atomicAdd(out.dpoints + i * PW + 3 * k + a, d);
+                } else {
+                    s_dp[threadIdx.x * PS + 3 * k + a] += d;
+                }
+            }
+        }
+    }
+    if (!ATOMIC) {
+        __syncthreads();
+        if (out.dpoints)
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) out.dpoints[i0 * PW + q] = s_dp[(q / PW) * PS + q % PW];
+        if (out.dsh)
+            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) out.dsh[i0 * SW + q] = s_dsh[(q / SW) * SS + q % SW];
+    }
+}
+
+}  // namespace
+
+template <int K, int STG>
+static void launch_pre_bwd_k(dim3 grid, cudaStream_t s, int deg, bool atomic, const ViewDesc *views_dev,
+                             const Settings &st, const float4 *records, const uint32_t *counts, const float4 *grads,
+                             const PreprocessGrads &g) {
+#define CS_PRE_BWD(D, A) \
+    k_preprocess_backward<K, D, A, STG><<<grid, PRE_THREADS, 0, s>>>(views_dev, st, records, counts, grads, g)
+    switch (deg * 2 + (atomic ? 1 : 0)) {
+        case 0: CS_PRE_BWD(0, false); break;
+        case 1: CS_PRE_BWD(0, true); break;
+        case 2: CS_PRE_BWD(1, false); break;
+        case 3: CS_PRE_BWD(1, true); break;
+        case 4: CS_PRE_BWD(2, false); break;
+        case 5: CS_PRE_BWD(2, true); break;
+        case 6: CS_PRE_BWD(3, false); break;
+        default: CS_PRE_BWD(3, true); break;
+    }
+#undef CS_PRE_BWD
+}
+
+template <int K>
+static void launch_pre_bwd_ks(dim3 grid, cudaStream_t s, int storage, int deg, bool atomic,
+                              const ViewDesc *views_dev, const Settings &st, const float4 *records,
+                              const uint32_t *counts, const float4 *grads, const PreprocessGrads &g) {
+    if (storage == CS_STORE_F16)
+        launch_pre_bwd_k<K, CS_STORE_F16>(grid, s, deg, atomic, views_dev, st, records, counts, grads, g);
+    else if (storage == CS_STORE_BF16)
+        launch_pre_bwd_k<K, CS_STORE_BF16>(grid, s, deg, atomic, views_dev, st, records, counts, grads, g);
+    else
+        launch_pre_bwd_k<K, CS_STORE_F32>(grid, s, deg, atomic, views_dev, st, records, counts, grads, g);
+}
+
+cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k, int sh_degree,
+                                       int storage, const Settings &st, const float4 *records, const uint32_t *counts,
+                                       const float4 *grad_records, const PreprocessGrads &g, bool atomic,
+                                       cudaStream_t s) {
+    if (max_n <= 0 || n_views <= 0) return cudaSuccess;
+    if (sh_degree < 0 || sh_degree > 3) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((max_n + PRE_THREADS - 1) / PRE_THREADS), (unsigned)n_views);
+    switch (k) {
+        case 3:
+            launch_pre_bwd_ks<3>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        case 4:
+            launch_pre_bwd_ks<4>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        case 5:
+            launch_pre_bwd_ks<5>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        case 6:
+            launch_pre_bwd_ks<6>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        case 7:
+            launch_pre_bwd_ks<7>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        case 8:
+            launch_pre_bwd_ks<8>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

@@ -84,9 +84,9 @@ struct cs_server {
         const double px = (double)c.width * c.height;
         const double pairs = s.pairs_per_convex * (double)s.sc.n * (px / (1920.0 * 1080.0)) + 64.0;
         const double tiles = (double)((c.width + 15) / 16) * ((c.height + 15) / 16);
-        // records, keys, counts, rects, sort temporaries; pairs and their sort buffers; per pixel
+        // records, keys, counts, rects, tile-test radii, sort temporaries; pairs and their sort buffers; per pixel
         // T_final and last contributor; tile ranges
-        return (size_t)((double)s.sc.n * 176.0 + pairs * 16.0 + px * 8.0 + tiles * 8.0 + 4096.0);
+        return (size_t)((double)s.sc.n * 180.0 + pairs * 16.0 + px * 8.0 + tiles * 8.0 + 4096.0);
     }
 
     void complete_locked(const Request &r, cs_status st, int batch, Clock::time_point now) {
@@ -169,7 +169,7 @@ void cs_server::run_worker() {
                 fill_view(vd, r.cam);
                 vd.points = sc.points; vd.delta = sc.delta; vd.sigma = sc.sigma;
                 vd.opacity = sc.opacity; vd.sh = sc.sh;
-                vd.n = sc.n; vd.k = sc.k; vd.sh_degree = sc.sh_degree;
+                vd.n = sc.n; vd.k = sc.k; vd.sh_degree = sc.sh_degree; vd.activation = sc.activation; vd.storage = sc.storage;
                 vd.image = r.image;
                 vd.t_final = nullptr;
                 b->weighted_views += (double)sc.n * ((double)r.cam.width * r.cam.height / (1920.0 * 1080.0));

@@ -16,6 +16,7 @@
 // digit-major histogram, stable scatter).  Ranks inside a block come from warp-level key matching
 // (__match_any_sync) over warp-striped runs of keys, so the scatter is stable.
 #include "cs_common.cuh"
+#include "cs_spec_math.cuh"
 
 namespace cs {
 namespace {
@@ -254,25 +255,89 @@ __global__ void k_view_keys(const ViewDesc *__restrict__ views, int n_views, con
 }
 
 // pair key = view << local_bits | tile index within the view (row major)
+// Emits the pairs of record sorted[j] at offsets[j]: every tile of its rectangle when all are kept
+// (count == area), else the tiles the exact test keeps, tested by the thread itself for small
+// rectangles and by the whole warp, 32 tiles at a time, for large ones.
 __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
-                       const uint2 *__restrict__ rects, int64_t n_records, int local_bits, uint32_t *__restrict__ keys,
-                       uint32_t *__restrict__ vals) {
+                       const uint2 *__restrict__ rects, const float4 *__restrict__ records,
+                       const float *__restrict__ radii, int64_t n_records, int local_bits,
+                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_records) return;
-    const uint32_t r = sorted[j];
-    if (counts[r] == 0) return;
-    const uint2 rc = rects[r];
-    const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-    const int v = view_of_record(views, n_views, r);
-    const uint32_t hi = (uint32_t)v << local_bits, tiles_x = (uint32_t)views[v].tiles_x;
-    uint32_t o = offsets[j];
-    for (uint32_t ty = ty0; ty <= ty1; ++ty)
-        for (uint32_t tx = tx0; tx <= tx1; ++tx) {
-            keys[o] = hi | (ty * tiles_x + tx);
-            vals[o] = r;
-            ++o;
+    const int lane = threadIdx.x & 31;
+    uint32_t r = 0, cnt = 0, area = 0, o = 0, hi = 0, tiles_x = 0;
+    uint2 rc = make_uint2(0, 0);
+    if (j < n_records) {
+        r = sorted[j];
+        cnt = counts[r];
+        if (cnt != 0) {
+            rc = rects[r];
+            area = ((rc.x >> 16) - (rc.x & 0xffffu) + 1) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1);
+            const int v = view_of_record(views, n_views, r);
+            hi = (uint32_t)v << local_bits;
+            tiles_x = (uint32_t)views[v].tiles_x;
+            o = offsets[j];
         }
+    }
+    const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
+    const bool coop = cnt != 0 && cnt != area && area > (uint32_t)SAT_SERIAL_TILES;
+    if (cnt != 0 && cnt == area) {  // every tile of the rectangle
+        for (uint32_t ty = ty0; ty <= ty1; ++ty)
+            for (uint32_t tx = tx0; tx <= tx1; ++tx) {
+                keys[o] = hi | (ty * tiles_x + tx);
+                vals[o] = r;
+                ++o;
+            }
+    } else if (cnt != 0 && !coop) {  // small rectangle: the same exact test on the same record values
+        float w[REC_WORDS];
+        const float4 *rec = records + (size_t)r * (REC_WORDS / 4);
+#pragma unroll
+        for (int q = 0; q < REC_WORDS / 4; ++q) {
+            const float4 f = rec[q];
+            w[4 * q] = f.x; w[4 * q + 1] = f.y; w[4 * q + 2] = f.z; w[4 * q + 3] = f.w;
+        }
+        const int T = (int)hull_pack_count(__float_as_uint(w[R_HULL]));
+        const float rk = radii[r];
+        for (uint32_t ty = ty0; ty <= ty1; ++ty)
+            for (uint32_t tx = tx0; tx <= tx1; ++tx)
+                if (tile_kept(w + R_LINES, T, w[R_AX], w[R_AY], rk, (int)tx, (int)ty)) {
+                    keys[o] = hi | (ty * tiles_x + tx);
+                    vals[o] = r;
+                    ++o;
+                }
+    }
+    uint32_t pending = __ballot_sync(0xffffffffu, coop);
+    while (pending) {  // large rectangles: the warp tests 32 tiles at a time, kept ones in row-major order
+        const int src = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const uint32_t rs = __shfl_sync(0xffffffffu, r, src), hs = __shfl_sync(0xffffffffu, hi, src);
+        const uint32_t txs = __shfl_sync(0xffffffffu, tiles_x, src);
+        const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, src), ry = __shfl_sync(0xffffffffu, rc.y, src);
+        uint32_t os = __shfl_sync(0xffffffffu, o, src);
+        float w[REC_WORDS];
+        const float4 *rec = records + (size_t)rs * (REC_WORDS / 4);
+#pragma unroll
+        for (int q = 0; q < REC_WORDS / 4; ++q) {
+            const float4 f = rec[q];
+            w[4 * q] = f.x; w[4 * q + 1] = f.y; w[4 * q + 2] = f.z; w[4 * q + 3] = f.w;
+        }
+        const int T = (int)hull_pack_count(__float_as_uint(w[R_HULL]));
+        const float rk = radii[rs];
+        const uint32_t x0 = rx & 0xffffu, y0 = ry & 0xffffu;
+        const uint32_t wd = (rx >> 16) - x0 + 1, ar = wd * ((ry >> 16) - y0 + 1);
+        for (uint32_t base = 0; base < ar; base += 32) {
+            const uint32_t q = base + (uint32_t)lane;
+            const uint32_t tx = x0 + q % wd, ty = y0 + q / wd;
+            const bool keep = q < ar && tile_kept(w + R_LINES, T, w[R_AX], w[R_AY], rk, (int)tx, (int)ty);
+            const uint32_t ball = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const uint32_t at = os + (uint32_t)__popc(ball & ((1u << lane) - 1u));
+                keys[at] = hs | (ty * txs + tx);
+                vals[at] = rs;
+            }
+            os += (uint32_t)__popc(ball);
+        }
+    }
 }
 
 // [start, end) of every (view, tile) group of the sorted pairs, stored at the global tile index
@@ -353,11 +418,13 @@ cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint3
 }
 
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
-                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects, int64_t n_records,
-                              int local_bits, uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
+                              const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
+                              const float4 *records, const float *radii, int64_t n_records, int local_bits,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
     if (n_records <= 0) return cudaSuccess;
     k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
-                                                               rects, n_records, local_bits, pair_keys, pair_vals);
+                                                               rects, records, radii, n_records, local_bits,
+                                                               pair_keys, pair_vals);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -91,7 +91,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     fill_view(vd, *cam);
     vd.points = scene->points; vd.delta = scene->delta; vd.sigma = scene->sigma;
     vd.opacity = scene->opacity; vd.sh = scene->sh;
-    vd.n = scene->n; vd.k = scene->k; vd.sh_degree = scene->sh_degree;
+    vd.n = scene->n; vd.k = scene->k; vd.sh_degree = scene->sh_degree; vd.activation = scene->activation; vd.storage = scene->storage;
     vd.image = image;
     vd.t_final = t_final;
     vd.rec_base = 0;
@@ -108,6 +108,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     uint2 *rects = c.take<uint2>(CS_STATIC_MAX_CONVEXES);
     uint32_t *counts = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     float4 *bboxes = c.take<float4>(CS_STATIC_MAX_CONVEXES);
+    float *radii = c.take<float>(CS_STATIC_MAX_CONVEXES);
     uint32_t *ka = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *kb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *va = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *vb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *offsets = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
@@ -125,7 +126,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
 
     e = cudaMemcpyAsync(views_dev, &vd, sizeof vd, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
-        PreprocessOut po{records, depth_keys, rects, counts, bboxes};
+        PreprocessOut po{records, depth_keys, rects, counts, bboxes, radii};
         e = launch_preprocess(views_dev, &vd, 1, R, scene->k, s, po, stream);
     }
     bool in_b = false;
@@ -142,7 +143,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
         return fail(CS_ERR_BUDGET, "cs_forward_static: %llu tile pairs exceed the static limit of %d", P,
                     CS_STATIC_MAX_PAIRS);
     const int local_bits = bits_for_tiles(tiles);
-    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, R, local_bits, pk, pv, stream);
+    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, R, local_bits, pk, pv, stream);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);
     const uint32_t *keys = in_b ? pk2 : pk;

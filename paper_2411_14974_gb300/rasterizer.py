@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import math
 from typing import Optional, Sequence
 
 import numpy as np
@@ -30,6 +31,7 @@ class Settings:
     bg: tuple = (0.0, 0.0, 0.0)
     dist_mode: int = 0
     dist_power: float = 1.0
+    tile_test: int = 0  # 1: exact tile test against the offset hull (tighter binning)
 
     def struct(self) -> B.CsSettings:
         s = B.CsSettings()
@@ -37,6 +39,7 @@ class Settings:
         for i in range(3):
             s.bg[i] = float(self.bg[i])
         s.dist_mode, s.dist_power = int(self.dist_mode), float(self.dist_power)
+        s.tile_test = int(self.tile_test)
         return s
 
 
@@ -85,6 +88,9 @@ class Context:
             pass
 
 
+_STORAGE = {torch.float32: 0, torch.float16: 1, torch.bfloat16: 2}
+
+
 @dataclasses.dataclass
 class SceneTensors:
     """Device tensors of a scene (float32, contiguous, on one CUDA device)."""
@@ -93,6 +99,7 @@ class SceneTensors:
     sigma: torch.Tensor    # [N]
     opacity: torch.Tensor  # [N]
     sh: torch.Tensor       # [N][(D+1)^2][3]
+    raw: bool = False      # delta, sigma, opacity hold log, log, logit (activated inside the forward)
 
     @property
     def sh_degree(self) -> int:
@@ -102,22 +109,37 @@ class SceneTensors:
             raise ValueError("sh must be [N][(D+1)^2][3]")
         return d
 
+    @property
+    def storage(self) -> int:
+        """cs_storage of the parameter tensors (all five share one dtype)."""
+        dt = self.points.dtype
+        if any(getattr(self, n).dtype != dt for n in ("delta", "sigma", "opacity", "sh")):
+            raise ValueError("points, delta, sigma, opacity and sh must share one dtype")
+        if dt not in _STORAGE:
+            raise ValueError("parameters must be float32, float16 or bfloat16")
+        return _STORAGE[dt]
+
     def struct(self) -> B.CsScene:
         s = B.CsScene()
+        storage = self.storage
         for name in ("points", "delta", "sigma", "opacity", "sh"):
             t = getattr(self, name)
-            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
-                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
             setattr(s, name, t.data_ptr() if t.numel() else None)
         s.n = int(self.points.shape[0])
         s.k = int(self.points.shape[1])
         s.sh_degree = self.sh_degree
+        s.activation = 1 if self.raw else 0
+        s.storage = storage
         return s
 
     @staticmethod
-    def from_numpy(scene, device="cuda") -> "SceneTensors":
-        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)
-        return SceneTensors(f(scene.points), f(scene.delta), f(scene.sigma), f(scene.opacity), f(scene.sh))
+    def from_numpy(scene, device="cuda", dtype=torch.float32) -> "SceneTensors":
+        """dtype float16 / bfloat16 stores the parameters in 16 bits (the paper's light model)."""
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device).to(dtype)
+        return SceneTensors(f(scene.points), f(scene.delta), f(scene.sigma), f(scene.opacity), f(scene.sh),
+                            bool(getattr(scene, "raw", False)))
 
 
 class State:
@@ -192,10 +214,9 @@ def backward(state: State, dL_dimage: torch.Tensor, grads: Optional[dict] = None
     """cs_backward: accumulate d(loss)/d(points, delta, sigma, opacity, sh) into ``grads``
     (zero tensors are created when not given)."""
     sc = state.scene
-    if grads is None:
-        grads = dict(points=torch.zeros_like(sc.points), delta=torch.zeros_like(sc.delta),
-                     sigma=torch.zeros_like(sc.sigma), opacity=torch.zeros_like(sc.opacity),
-                     sh=torch.zeros_like(sc.sh))
+    if grads is None:  # gradients are float32 whatever the parameter storage
+        z = lambda t: torch.zeros(t.shape, dtype=torch.float32, device=t.device)
+        grads = dict(points=z(sc.points), delta=z(sc.delta), sigma=z(sc.sigma), opacity=z(sc.opacity), sh=z(sc.sh))
     g = dL_dimage.contiguous()
     if g.dtype != torch.float32:
         g = g.float()
@@ -209,9 +230,9 @@ def backward(state: State, dL_dimage: torch.Tensor, grads: Optional[dict] = None
 
 class _Render(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, points, delta, sigma, opacity, sh, cams, settings):
+    def forward(ctx, points, delta, sigma, opacity, sh, cams, settings, raw):
         scene = SceneTensors(points.detach().contiguous(), delta.detach().contiguous(), sigma.detach().contiguous(),
-                             opacity.detach().contiguous(), sh.detach().contiguous())
+                             opacity.detach().contiguous(), sh.detach().contiguous(), raw)
         need = any(ctx.needs_input_grad[:5])
         image, _, state = forward(scene, cams, settings, keep_state=need)
         ctx.state = state
@@ -221,16 +242,223 @@ class _Render(torch.autograd.Function):
     def backward(ctx, dL_dimage):
         state = ctx.state
         g = backward(state, dL_dimage)
+        sc = state.scene
         state.release()
         ctx.state = None
-        return g["points"], g["delta"], g["sigma"], g["opacity"], g["sh"], None, None
+        out = [g[k].to(getattr(sc, k).dtype) for k in PARAMS]  # float32 gradients, in each input's dtype
+        return (*out, None, None, None)
 
 
-def render(points, delta, sigma, opacity, sh, cams, settings: Optional[Settings] = None) -> torch.Tensor:
+def render(points, delta, sigma, opacity, sh, cams, settings: Optional[Settings] = None,
+           raw: bool = False) -> torch.Tensor:
     """Differentiable render (Sec. 3.2, Eq. 4, 5, S1, S2): image [V][3][H][W] for len(cams) views.
 
-    delta, sigma, opacity are activated values (> 0, > 0, in (0, 1])."""
-    return _Render.apply(points, delta, sigma, opacity, sh, list(cams), settings or Settings())
+    delta, sigma, opacity are activated values (> 0, > 0, in (0, 1]), or with raw=True the
+    training parameters log delta, log sigma, logit opacity (Sec. 3.3), activated in the forward."""
+    return _Render.apply(points, delta, sigma, opacity, sh, list(cams), settings or Settings(), bool(raw))
+
+
+# ---- training step (Sec. 3.3) -------------------------------------------------------------------
+PARAMS = ("points", "delta", "sigma", "opacity", "sh")
+
+
+def _ctx_of(t: torch.Tensor) -> Context:
+    return Context.get(t.device.index if t.device.index is not None else torch.cuda.current_device())
+
+
+def loss_l1_dssim(image: torch.Tensor, target: torch.Tensor, lam: float = 0.2, grad: bool = True,
+                  loss_out: Optional[torch.Tensor] = None, dL_dimage: Optional[torch.Tensor] = None):
+    """cs_loss_l1_dssim: (1 - lam) L1 + lam D-SSIM of images [V][3][H][W] (Eq. 6 without the mask
+    term).  Returns (loss as a one-element device tensor, dL/dimage or None)."""
+    if image.shape != target.shape or image.dim() != 4 or image.shape[1] != 3:
+        raise ValueError("image and target must both be [V][3][H][W]")
+    for t in (image, target):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("image and target must be contiguous float32 CUDA tensors")
+    V, _, H, W = image.shape
+    if loss_out is None:
+        loss_out = torch.empty(1, device=image.device, dtype=torch.float32)
+    if grad and dL_dimage is None:
+        dL_dimage = torch.empty_like(image)
+    code = B.lib().cs_loss_l1_dssim(_ctx_of(image).handle, image.data_ptr(), target.data_ptr(), V, H, W, float(lam),
+                                    loss_out.data_ptr(), dL_dimage.data_ptr() if grad else None,
+                                    _stream_ptr(image.device))
+    B.check(code, "cs_loss_l1_dssim")
+    return loss_out, (dL_dimage if grad else None)
+
+
+def adam_step(groups: Sequence[dict], step: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15,
+              zero_grad: bool = True):
+    """cs_adam_step over groups of dict(param, grad, m, v, lr[, grad_abs_sum]) (float32 CUDA tensors
+    of equal size), all in one launch."""
+    if len(groups) > B.ADAM_MAX_GROUPS:
+        raise ValueError(f"at most {B.ADAM_MAX_GROUPS} groups")
+    arr = (B.CsAdamGroup * max(1, len(groups)))()
+    dev = None
+    for i, g in enumerate(groups):
+        p = g["param"]
+        dev = p.device
+        for name in ("param", "grad", "m", "v", "grad_abs_sum"):
+            t = g.get(name)
+            if t is None:
+                continue
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() != p.numel():
+                raise ValueError(f"group {i}: {name} must be a contiguous float32 CUDA tensor like param")
+            setattr(arr[i], name, t.data_ptr() if t.numel() else None)
+        arr[i].n = p.numel()
+        arr[i].lr = float(g["lr"])
+    st = B.CsAdamSettings(float(beta1), float(beta2), float(eps), int(bool(zero_grad)))
+    if dev is None:
+        return
+    code = B.lib().cs_adam_step(_ctx_of(groups[0]["param"]).handle, arr, len(groups), ctypes.byref(st), int(step),
+                                _stream_ptr(dev))
+    B.check(code, "cs_adam_step")
+
+
+@dataclasses.dataclass
+class RefineSettings:
+    """Adaptive refinement settings (supplement Sec. A).  The paper gives the split threshold, the
+    scale-down (0.7 indoor, 0.6 outdoor) and the opacity prune level; how much sigma rises and
+    opacity falls for split children, and the size bound, are settings."""
+    split_threshold: float = 4e-6
+    split_scale: float = 0.7
+    split_sigma_scale: float = 1.5
+    split_opacity_scale: float = 0.5
+    prune_opacity: float = 0.03
+    prune_size: float = float("inf")
+
+    def struct(self) -> B.CsRefineSettings:
+        return B.CsRefineSettings(self.split_threshold, self.split_scale, self.split_sigma_scale,
+                                  self.split_opacity_scale, self.prune_opacity, self.prune_size)
+
+
+def _param_arrays(d: Optional[dict]):
+    if d is None:
+        return None
+    a = B.CsParamArrays()
+    for k in PARAMS:
+        t = d[k]
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{k} must be a contiguous float32 CUDA tensor")
+        setattr(a, k, t.data_ptr() if t.numel() else None)
+    return a
+
+
+def refine(params: dict, sigma_grad_abs: torch.Tensor, window_steps: int, settings: Optional[RefineSettings] = None,
+           m: Optional[dict] = None, v: Optional[dict] = None, decisions: bool = False):
+    """cs_refine: split / prune raw parameters (dict of PARAMS tensors) and their Adam moments.
+    Returns (new params, new m or None, new v or None, decisions tensor or None)."""
+    settings = settings or RefineSettings()
+    pts = params["points"]
+    n, k = int(pts.shape[0]), int(pts.shape[1])
+    nb = int(params["sh"].shape[1])
+    deg = int(round(nb ** 0.5)) - 1
+    dev = pts.device
+    cap = n * k
+    alloc = lambda: {key: torch.empty((cap,) + tuple(params[key].shape[1:]), device=dev) for key in PARAMS}
+    out, om, ov = alloc(), (alloc() if m is not None else None), (alloc() if m is not None else None)
+    dec = torch.empty(n, dtype=torch.int32, device=dev) if decisions else None
+    n_out = ctypes.c_int64()
+    st = settings.struct()
+    a_in, a_m, a_v = _param_arrays(params), _param_arrays(m), _param_arrays(v)
+    a_out, a_om, a_ov = _param_arrays(out), _param_arrays(om), _param_arrays(ov)
+    ref = lambda x: ctypes.byref(x) if x is not None else None
+    code = B.lib().cs_refine(_ctx_of(pts).handle, n, k, deg, ref(a_in), ref(a_m), ref(a_v),
+                             sigma_grad_abs.data_ptr() if n else None, int(window_steps), ctypes.byref(st), cap,
+                             ref(a_out), ref(a_om), ref(a_ov), dec.data_ptr() if dec is not None else None,
+                             ctypes.byref(n_out), _stream_ptr(dev))
+    B.check(code, "cs_refine")
+    cut = lambda d: None if d is None else {key: d[key][:n_out.value].contiguous() for key in PARAMS}
+    return cut(out), cut(om), cut(ov), dec
+
+
+@dataclasses.dataclass
+class TrainConfig:
+    """Optimiser settings of Sec. 3.3 and the supplementary hyper-parameters.  The paper gives the
+    rates for delta, sigma and the points (5e-4 decaying exponentially to 5e-6); opacity and SH
+    rates are not given and are settings here."""
+    lr_points: float = 5e-4
+    lr_points_final: float = 5e-6
+    lr_decay_steps: int = 30_000
+    lr_delta: float = 0.005
+    lr_sigma: float = 0.0045
+    lr_opacity: float = 0.025
+    lr_sh: float = 0.0025
+    lam: float = 0.2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+    def points_lr(self, step: int) -> float:
+        """Log-linear decay from lr_points at step 1 to lr_points_final at lr_decay_steps."""
+        s = min(max(step - 1, 0) / max(self.lr_decay_steps - 1, 1), 1.0)
+        return math.exp((1.0 - s) * math.log(self.lr_points) + s * math.log(self.lr_points_final))
+
+
+class Trainer:
+    """One optimisation step per call, all on the device: forward on the raw training parameters
+    (activations inside the preprocess), L1 + D-SSIM loss against the target, backward into the
+    raw-parameter gradients, then one fused Adam launch over the five parameter groups.  The
+    sigma group also accumulates |dL/dsigma| per convex (the split statistic)."""
+
+    def __init__(self, scene: SceneTensors, settings: Optional[Settings] = None, config: Optional[TrainConfig] = None):
+        if not scene.raw:
+            raise ValueError("Trainer optimises raw parameters: SceneTensors(raw=True)")
+        if scene.storage != 0:
+            raise ValueError("Trainer optimises float32 parameters (16-bit storage is for rendering)")
+        self.scene = scene
+        self.settings = settings or Settings()
+        self.config = config or TrainConfig()
+        self.grads = {k: torch.zeros_like(getattr(scene, k)) for k in PARAMS}
+        self.m = {k: torch.zeros_like(getattr(scene, k)) for k in PARAMS}
+        self.v = {k: torch.zeros_like(getattr(scene, k)) for k in PARAMS}
+        self.sigma_grad_abs = torch.zeros_like(scene.sigma)
+        self.step_count = 0
+        self._last_refine = 0
+        self._image = None
+        self._dL = None
+        self.loss = torch.zeros(1, device=scene.points.device)
+
+    def groups(self, step: int) -> list:
+        c = self.config
+        lr = dict(points=c.points_lr(step), delta=c.lr_delta, sigma=c.lr_sigma, opacity=c.lr_opacity, sh=c.lr_sh)
+        out = []
+        for k in PARAMS:
+            g = dict(param=getattr(self.scene, k), grad=self.grads[k], m=self.m[k], v=self.v[k], lr=lr[k])
+            if k == "sigma":
+                g["grad_abs_sum"] = self.sigma_grad_abs
+            out.append(g)
+        return out
+
+    def refine(self, settings: Optional[RefineSettings] = None, window_steps: Optional[int] = None):
+        """Split and prune (cs_refine) with the sigma statistic gathered since the last refinement;
+        the scene, moments and gradients are replaced and the statistic restarts."""
+        window = window_steps if window_steps is not None else max(self.step_count - self._last_refine, 1)
+        params = {k: getattr(self.scene, k) for k in PARAMS}
+        out, m, v, dec = refine(params, self.sigma_grad_abs, window, settings, self.m, self.v, decisions=True)
+        for k in PARAMS:
+            setattr(self.scene, k, out[k])
+        self.m, self.v = m, v
+        self.grads = {k: torch.zeros_like(out[k]) for k in PARAMS}
+        self.sigma_grad_abs = torch.zeros_like(out["sigma"])
+        self._last_refine = self.step_count
+        return dec
+
+    def step(self, cams: Sequence, target: torch.Tensor) -> torch.Tensor:
+        """target: [V][3][H][W] float32 on the scene's device.  Returns the loss (device tensor)."""
+        V = len(cams)
+        H, W = int(cams[0].height), int(cams[0].width)
+        if self._image is None or tuple(self._image.shape) != (V, 3, H, W):
+            self._image = torch.empty((V, 3, H, W), device=self.scene.points.device)
+            self._dL = torch.empty_like(self._image)
+        _, _, st = forward(self.scene, cams, self.settings, keep_state=True, image=self._image)
+        loss_l1_dssim(self._image, target, self.config.lam, True, self.loss, self._dL)
+        backward(st, self._dL, self.grads)
+        st.release()
+        self.step_count += 1
+        c = self.config
+        adam_step(self.groups(self.step_count), self.step_count, c.beta1, c.beta2, c.eps, zero_grad=True)
+        return self.loss
 
 
 # ---- instrumentation and host-buffer entry points ---------------------------------------------
@@ -281,6 +509,8 @@ def step_host(scene_host: dict, sh_degree: int, cams: Sequence, settings: Option
     sc.n = int(scene_host["points"].shape[0])
     sc.k = int(scene_host["points"].shape[1])
     sc.sh_degree = int(sh_degree)
+    sc.activation = 1 if scene_host.get("raw", False) else 0
+    sc.storage = _STORAGE[scene_host["points"].dtype]
     s = (settings or Settings()).struct()
     g = grads_host or {}
     ptr = lambda t: t.data_ptr() if t is not None else None

@@ -92,6 +92,44 @@ def test_gradient_settings_variants(kw):
     compare(got, ref, refp)
 
 
+def test_gradient_raw_parameters():
+    """With CS_ACT_EXP_SIGMOID the backward returns gradients w.r.t. log delta, log sigma and
+    logit opacity: the oracle's activated-scene gradient times exp' = exp and sigmoid' = o (1 - o)."""
+    raw = _blob(4, deg=1).as_raw()
+    act = oracle.activate(raw)
+    cam = syn.blob_camera(64, 64)
+    G = np.random.default_rng(4).uniform(-1, 1, (1, 3, 64, 64))
+    st = oracle_settings()
+    ref = oracle.raw_gradients(raw, oracle.backward_image(act, cam, st, G[0]))
+    refp = [oracle.raw_gradients(raw, oracle.backward_image(act, cam, st, G[0], perturb_seed=s)) for s in (1, 2)]
+    got, _ = gpu_grads(raw, [cam], G)
+    compare(got, ref, refp)
+
+
+def test_gradient_16bit_storage():
+    """Float32 gradients of a float16-stored scene equal the oracle's on the widened values."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = _blob(6, deg=2)
+    wide = sc.copy()
+    for name in FIELDS:
+        setattr(wide, name, np.ascontiguousarray(
+            torch.as_tensor(getattr(sc, name)).to(torch.float16).to(torch.float32).numpy()))
+    cam = syn.blob_camera(64, 64)
+    G = np.random.default_rng(6).uniform(-1, 1, (1, 3, 64, 64))
+    st = oracle_settings()
+    ref = oracle.backward_image(wide, cam, st, G[0])
+    refp = [oracle.backward_image(wide, cam, st, G[0], perturb_seed=s) for s in (1, 2)]
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev, dtype=torch.float16)
+    _, _, state = cs.forward(t, [cam], cs.Settings(), keep_state=True)
+    g = cs.backward(state, torch.as_tensor(np.ascontiguousarray(G, np.float32), device=dev))
+    torch.cuda.synchronize()
+    assert all(v.dtype == torch.float32 for v in g.values())
+    compare({k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}, ref, refp)
+    state.release()
+
+
 def test_gradient_surface_sh3():
     sc = syn.surface_scene(21, n=20_000, sh_degree=3)
     cam = syn.sphere_cameras(1, 120, 96, 4.0, seed=22)[0]

@@ -34,8 +34,7 @@ def check_discrete(state, sc, cam, rec_base=0, tile_base=0, **kw):
     assert (dk[~vis] == 0xFFFFFFFF).all()
     assert (hulls == oracle.pack_hull(disc)).all(), "hull vertex indices differ"
     assert (rects[vis] == _pack_rect(disc["rect"][vis])).all(), "tile ranges differ"
-    r = disc["rect"][vis].astype(np.int64)
-    assert (cnt[vis] == (r[:, 2] - r[:, 0] + 1) * (r[:, 3] - r[:, 1] + 1)).all()
+    assert (cnt[vis] == disc["count"][vis]).all(), "kept-tile counts of the exact tile test differ"
     return disc
 
 
@@ -89,6 +88,31 @@ def test_blob1k_128_discrete_and_order(seed):
     img, tf, state, _ = P.gpu_render(sc, cams)
     disc = check_discrete(state, sc, cams[0])
     check_pairs(state, [disc], cams)
+
+
+@pytest.mark.parametrize("scene", ["blob", "surface", "clustered"])
+def test_exact_tile_test_parity(scene):
+    """tile_test = 1: the kept tiles of every convex (per thread for small rectangles, per warp for
+    large ones, in the preprocess count and again in the emission) equal the oracle's bit for bit,
+    and the image is unchanged within the parity bar."""
+    if scene == "blob":
+        sc, cam = syn.workload("blob1k_128", seed=5)[0], syn.blob_camera()
+    elif scene == "surface":
+        sc, cam = syn.surface_scene(31, n=30_000, sh_degree=1), syn.sphere_cameras(1, 320, 240, 3.0, seed=32)[0]
+    else:
+        sc = syn.surface_scene(33, n=30_000, sh_degree=0, clustered_fraction=0.9)
+        sc.points = (sc.points.mean(axis=1, keepdims=True) + 3.0 * (sc.points - sc.points.mean(axis=1, keepdims=True))).astype(np.float32)
+        cam = syn.sphere_cameras(1, 480, 360, 3.0, seed=34)[0]
+    img, tf, state, _ = P.gpu_render(sc, [cam], tile_test=1)
+    disc = check_discrete(state, sc, cam, tile_test=1)
+    area = (disc["rect"][:, 2] - disc["rect"][:, 0] + 1) * (disc["rect"][:, 3] - disc["rect"][:, 1] + 1)
+    vis = disc["visible"] == 1
+    assert (disc["count"][vis] < area[vis]).any()  # the test removes tiles here
+    if scene == "clustered":
+        assert (area[vis] > 8).sum() > 100  # the warp-cooperative path runs
+    check_pairs(state, [disc], [cam])
+    ref, ill = P.oracle_reference(sc, cam, tile_test=1)
+    check_image(img[0], ref, ill, max_ill=0.08)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -191,6 +215,53 @@ def test_nonfinite_and_invalid_parameters_are_culled():
     disc = check_discrete(state, sc, cam)
     assert not disc["visible"][:4].any()
     check_image(img[0], ref, ill)
+
+
+def test_raw_parameters_are_activated_in_the_forward():
+    """CS_ACT_EXP_SIGMOID: the forward activates log delta, log sigma and logit opacity (Sec. 3.3)
+    in the binary32 definition both sides share, so the discrete spec stays bit-exact; raw values
+    beyond the exp range make delta/sigma infinite or zero and opacity 0, which culls."""
+    raw = syn.workload("blob1k_128", seed=3)[0].as_raw()
+    raw.delta[0], raw.sigma[1], raw.delta[2], raw.opacity[3] = 100.0, -100.0, 88.9, -300.0
+    cam = syn.blob_camera()
+    act = oracle.activate(raw)
+    img, tf, state, _ = P.gpu_render(raw, [cam])
+    disc = check_discrete(state, act, cam)
+    assert not disc["visible"][:4].any()
+    check_pairs(state, [disc], [cam])
+    ref, ill = P.oracle_reference(act, cam)
+    check_image(img[0], ref, ill)
+
+
+def _widened(sc, dtype):
+    """The scene as the 16-bit storage holds it, widened back to float32 (exactly)."""
+    import torch
+    out = sc.copy()
+    for name in ("points", "delta", "sigma", "opacity", "sh"):
+        t = torch.as_tensor(getattr(sc, name)).to(dtype).to(torch.float32)
+        setattr(out, name, np.ascontiguousarray(t.numpy()))
+    return out
+
+
+@pytest.mark.parametrize("dtype_name", ["float16", "bfloat16"])
+def test_light_16bit_storage(dtype_name):
+    """16-bit parameter storage (the light model): the kernels widen every value on load, so the
+    render equals the oracle's on the widened float32 values, the discrete spec bit for bit."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    dtype = getattr(torch, dtype_name)
+    for sc, cam in ((syn.workload("blob1k_128", seed=4)[0], syn.blob_camera()),
+                    (syn.surface_scene(13, n=20_000, sh_degree=3), syn.sphere_cameras(1, 160, 120, 4.0, seed=14)[0])):
+        wide = _widened(sc, dtype)
+        t = cs.SceneTensors.from_numpy(sc, torch.device("cuda:0"), dtype=dtype)
+        assert t.storage == (1 if dtype == torch.float16 else 2)
+        img, tf, state = cs.forward(t, [cam], cs.Settings(), keep_state=True)
+        torch.cuda.synchronize()
+        disc = check_discrete(state, wide, cam)
+        check_pairs(state, [disc], [cam])
+        ref, ill = P.oracle_reference(wide, cam)
+        check_image(img[0].cpu().numpy().astype(np.float64), ref, ill, max_ill=0.08)
+        state.release()
 
 
 def test_multi_view_equals_single_views():

@@ -70,6 +70,8 @@ def test_culling_rules():
 
 
 def _conservative(sc, cam, st=None):
+    """Every pixel with binary64 alpha >= tau lies in the rectangle and in a tile the exact tile
+    test keeps; returns (convexes reaching tau, tiles the test removed from the rectangles)."""
     st = st or oracle.settings()
     d = oracle.discrete(sc, cam, st)
     bb = oracle.alpha_support(sc, cam, st)
@@ -79,13 +81,21 @@ def _conservative(sc, cam, st=None):
     b = bb[has]
     assert (b[:, 0] // 16 >= r[:, 0]).all() and (b[:, 2] // 16 <= r[:, 2]).all()
     assert (b[:, 1] // 16 >= r[:, 1]).all() and (b[:, 3] // 16 <= r[:, 3]).all()
-    return has.sum()
+    mask = oracle.alpha_tile_mask(sc, cam, st)
+    for i in np.nonzero(has)[0]:
+        kept = set(d["tiles"][d["tile_offsets"][i]:][:d["count"][i]].tolist())
+        need = set(np.nonzero(mask[i])[0].tolist())
+        assert need <= kept, (i, sorted(need - kept))
+    vis = d["visible"] == 1
+    area = (d["rect"][vis, 2] - d["rect"][vis, 0] + 1) * (d["rect"][vis, 3] - d["rect"][vis, 1] + 1)
+    return has.sum(), int(area.sum() - d["count"][vis].sum())
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_tile_range_conservative_blob(seed):
     sc, cams = syn.workload("blob1k_128", seed=seed)
-    assert _conservative(sc, cams[0]) > 500
+    assert _conservative(sc, cams[0])[0] > 500
+    assert _conservative(sc, cams[0], oracle.settings(tile_test=1))[0] > 500
 
 
 def test_tile_range_conservative_soft_and_sharp():
@@ -96,9 +106,43 @@ def test_tile_range_conservative_soft_and_sharp():
     sc.delta = np.exp(rng.uniform(math.log(0.02), math.log(200.0), sc.n)).astype(np.float32)
     sc.sigma = np.exp(rng.uniform(math.log(0.001), math.log(20.0), sc.n)).astype(np.float32)
     sc.opacity = rng.uniform(0.005, 1.0, sc.n).astype(np.float32)
+    removed = 0
     for st in (oracle.settings(), oracle.settings(tau=0.05), oracle.settings(dist_power=2.0),
                oracle.settings(dist_mode=1, dist_power=0.5)):
-        assert _conservative(sc, cam, st) > 50
+        n, rm = _conservative(sc, cam, st)
+        assert n > 50 and rm == 0  # without the tile test every tile of the rectangle is kept
+    for st in (oracle.settings(tile_test=1), oracle.settings(tau=0.05, tile_test=1),
+               oracle.settings(dist_power=2.0, tile_test=1), oracle.settings(dist_mode=1, dist_power=0.5, tile_test=1)):
+        n, rm = _conservative(sc, cam, st)
+        assert n > 50
+        removed += rm
+    assert removed > 0  # the exact tile test is not vacuous on these shapes
+
+
+def test_exact_tile_test_drops_tiles_a_thin_diagonal_convex_misses():
+    """A thin sharp convex along the image diagonal: its rectangle spans many tiles, most of which
+    lie off the diagonal and are dropped; the tiles along it are kept."""
+    cam = syn.blob_camera(160, 160)
+    z, f = 4.0, cam.fx
+    # a sliver from pixel (8, 8) to (152, 152), about 1 px wide
+    a = np.array([8.0, 8.0]) - 80.0
+    b = np.array([152.0, 152.0]) - 80.0
+    w = np.array([0.7, -0.7])
+    quad = [a, b, b + w, a + w]
+    pts = np.array([[q[0] * z / f, q[1] * z / f, z] for q in quad] + [[a[0] * z / f, a[1] * z / f, z]] * 2)
+    sc = syn.Scene(pts[None].astype(np.float32) - np.array([0, 0, 4.0], np.float32),
+                   np.array([5.0], np.float32), np.array([5.0], np.float32), np.array([0.9], np.float32),
+                   np.zeros((1, 1, 3), np.float32), 0)
+    st = oracle.settings(tile_test=1)
+    d = oracle.discrete(sc, cam, st)
+    assert d["visible"][0] == 1
+    x0, y0, x1, y1 = d["rect"][0]
+    area = (x1 - x0 + 1) * (y1 - y0 + 1)
+    assert area >= 80 and d["count"][0] <= 0.4 * area
+    kept = set(d["tiles"][:d["count"][0]].tolist())
+    assert all((t * 10 + t) in kept for t in range(1, 9))  # the diagonal tiles (ty = tx)
+    _conservative(sc, cam, st)
+    assert oracle.discrete(sc, cam)["count"][0] == area  # without the test: the whole rectangle
 
 
 def test_sh_orthonormal_by_quadrature():
