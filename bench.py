@@ -378,6 +378,26 @@ def stress_bench(dev_index, steps=3, warmup=2, tile_test=0):
                 evaluated_pairs=wc["forward"]["passed"], fractions_at_2070mhz=frac)
 
 
+def _profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when that summary
+    is for another kernel or the kernel's sources changed since the counters were taken."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(root, "profiles", "blend_surface1M_1920x1080.md")).read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and not line.startswith("|"))
+    if fields.get("traffic_kernel") != kernel:
+        return None
+    for name, rel in (("blend.cu", "paper_2411_14974_gb300/csrc/blend.cu"),
+                      ("cs_common.cuh", "paper_2411_14974_gb300/csrc/cs_common.cuh")):
+        with open(os.path.join(root, rel), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != fields.get(f"source_sha1 {name}"):
+                return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 def _hbm_peak():
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
@@ -536,7 +556,9 @@ def run_ours(args):
                                achieved=achieved, peak=mufu_peak, unit="Gop/s (MUFU)", frac=achieved / mufu_peak,
                                fp32_ginstr_s=fp32 / t / 1e9, fp32_peak_ginstr_s=fp32_peak,
                                fp32_frac=fp32 / t / 1e9 / fp32_peak, peak_clock_mhz=mhz,
-                               work_per_launch=tot, traffic=None)
+                               work_per_launch=tot,
+                               traffic=_profiled_traffic(f"k_blend_{'forward' if dom == 'blend' else 'backward'}"),
+                               traffic_unit="bytes per launch (ncu dram read + write)")
         # end to end through the host-buffer C-ABI call: scene and cotangent uploaded, image and
         # gradients read back, every step
         pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory()
