@@ -110,30 +110,27 @@ struct PairTerms {
 };
 
 // returns 0 when the line pre-test rejects the pair, 1 when alpha < tau, 2 when it contributes;
-// HALF selects the 8x4 origin (0 upper, 1 lower) the pixel's local coordinates refer to
-template <int HALF>
+// HALF selects the 8x4 origin (0 upper, 1 lower) the pixel's local coordinates refer to; NT is
+// the record's number of hull lines (the callers branch on it once per record, uniformly across
+// the warp, so the line loops carry no per-line guards)
+template <int HALF, int NT>
 __device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float lx, float ly, const Settings &st,
                                          PairTerms &p) {
     const float4 h0 = rec[0];
-    const int T = __float_as_int(h0.w);
-    float s[KMAX];
+    float s[NT];
     float m = -__int_as_float(0x7f800000);
 #pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-        if (t < T) {
-            const float4 L = rec[3 + t];
-            s[t] = fmaf(L.x, lx, fmaf(L.y, ly, HALF ? L.w : L.z));
-            m = fmaxf(m, s[t]);
-        }
+    for (int t = 0; t < NT; ++t) {
+        const float4 L = rec[3 + t];
+        s[t] = fmaf(L.x, lx, fmaf(L.y, ly, HALF ? L.w : L.z));
+        m = fmaxf(m, s[t]);
     }
     if (m > h0.y) return 0;
     float S = 0.f;
 #pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-        if (t < T) {
-            p.e[t] = ex2(s[t] - m);
-            S += p.e[t];
-        }
+    for (int t = 0; t < NT; ++t) {
+        p.e[t] = ex2(s[t] - m);
+        S += p.e[t];
     }
     p.S = S;
     p.phi2 = m + lg2(S);
@@ -262,7 +259,15 @@ __global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsi
                 bits &= bits - 1;
                 const float4 *rec = wrec + j * SREC;
                 PairTerms p;
-                const int code = eval_pair<0>(rec, lx, ly, st, p);
+                int code;
+                switch (__float_as_int(rec[0].w)) {  // the record's line count, uniform across the warp
+                    case 3: code = eval_pair<0, 3>(rec, lx, ly, st, p); break;
+                    case 4: code = eval_pair<0, 4>(rec, lx, ly, st, p); break;
+                    case 5: code = eval_pair<0, 5>(rec, lx, ly, st, p); break;
+                    case 6: code = eval_pair<0, 6>(rec, lx, ly, st, p); break;
+                    case 7: code = eval_pair<0, 7>(rec, lx, ly, st, p); break;
+                    default: code = eval_pair<0, 8>(rec, lx, ly, st, p); break;
+                }
                 if (COUNT) count_pair(cnt, rec, code);
                 if (code != 2) continue;
                 const float4 c = rec[1];
@@ -291,8 +296,67 @@ __global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsi
     if (COUNT) flush_counts(counts, cnt);
 }
 
+// per-lane state of the backward's two pixels (rows r and r + 4 of the warp's 8x8 block)
+struct BwdPixels {
+    float Tc[2];               // transmittance behind the pair being undone
+    float G0[2], G1[2], G2[2];  // dL/dC
+    float S0[2], S1[2], S2[2];  // colour seen behind the current pair, times T
+    uint32_t last[2];          // pairs at or beyond this index did not contribute
+};
+
+// Undoes record rec (pair index idx, NT lines) for both pixels of the lane: recovers T in front
+// of the pair, accumulates the per-pixel gradient terms into v32, and returns whether any of the
+// two pixels received a contribution.
+template <int NT, bool COUNT>
+__device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint32_t idx, float lx, float ly,
+                                           const Settings &st, BwdPixels &q, float (&v32)[32],
+                                           unsigned long long (&cnt)[NCOUNT]) {
+    const float4 h0 = rec[0];
+    bool any_on = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (idx >= q.last[k]) continue;
+        PairTerms p;
+        const int code = k ? eval_pair<1, NT>(rec, lx, ly, st, p) : eval_pair<0, NT>(rec, lx, ly, st, p);
+        if (COUNT) count_pair(cnt, rec, code);
+        if (code != 2) continue;
+        any_on = true;
+        const float4 c = rec[1];
+        const float om = 1.0f - p.alpha;
+        const float inv = __frcp_rn(om);
+        const float Tn = q.Tc[k] * inv;  // transmittance in front of this pair
+        const float dalpha = q.G0[k] * (Tn * c.x - q.S0[k] * inv) + q.G1[k] * (Tn * c.y - q.S1[k] * inv) +
+                             q.G2[k] * (Tn * c.z - q.S2[k] * inv);
+        const float ta = Tn * p.alpha;
+        v32[G_RGB] += q.G0[k] * ta;
+        v32[G_RGB + 1] += q.G1[k] * ta;
+        v32[G_RGB + 2] += q.G2[k] * ta;
+        q.S0[k] = fmaf(ta, c.x, q.S0[k]);
+        q.S1[k] = fmaf(ta, c.y, q.S1[k]);
+        q.S2[k] = fmaf(ta, c.z, q.S2[k]);
+        q.Tc[k] = Tn;
+        if (p.oI < st.alpha_max) {
+            v32[G_OPA] += dalpha * p.I;
+            const float dI = dalpha * h0.z;
+            // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
+            const float dx = -dI * LN2 * p.z * p.I * p.I;
+            v32[G_SIG] += dx * p.phi2;
+            const float dphi2 = dx * h0.x * rcp(p.S);
+            const float ly8 = ly + 4.0f * k;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const float gt = dphi2 * p.e[t];
+                v32[3 * t] = fmaf(gt, lx, v32[3 * t]);
+                v32[3 * t + 1] = fmaf(gt, ly8, v32[3 * t + 1]);
+                v32[3 * t + 2] += gt;
+            }
+        }
+    }
+    return any_on;
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(BWD_THREADS) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
+__global__ void __launch_bounds__(BWD_THREADS, 4) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
     __shared__ float4 srec[BWD_THREADS / 32][32 * SREC];
@@ -313,8 +377,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_backward(BlendArgs a, con
     uint32_t *sidx = sidx_all[w];
 
     // pixel k of this lane is row (lane >> 3) of the upper (k = 0) or lower (k = 1) 8x4 half
-    float Tc[2], G0[2], G1[2], G2[2], S0[2], S1[2], S2[2];
-    uint32_t last[2];
+    BwdPixels q;
     unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, 0};
     const size_t hw = (size_t)vd.width * vd.height;
     const float *dl = dL_dimage + v * image_stride;
@@ -322,23 +385,23 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_backward(BlendArgs a, con
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int py = by + (lane >> 3) + 4 * k;
-        Tc[k] = 1.0f;
-        G0[k] = G1[k] = G2[k] = 0.f;
-        last[k] = 0;
+        q.Tc[k] = 1.0f;
+        q.G0[k] = q.G1[k] = q.G2[k] = 0.f;
+        q.last[k] = 0;
         if (px < vd.width && py < vd.height) {
             const size_t pix = (size_t)py * vd.width + px;
-            G0[k] = dl[pix];
-            G1[k] = dl[hw + pix];
-            G2[k] = dl[2 * hw + pix];
-            Tc[k] = vd.t_final[pix];
-            last[k] = vd.n_last[pix];
+            q.G0[k] = dl[pix];
+            q.G1[k] = dl[hw + pix];
+            q.G2[k] = dl[2 * hw + pix];
+            q.Tc[k] = vd.t_final[pix];
+            q.last[k] = vd.n_last[pix];
             cnt[5]++;
         }
         // colour seen behind the current pair: T_after * (its colour) summed from the back
-        S0[k] = Tc[k] * st.bg[0];
-        S1[k] = Tc[k] * st.bg[1];
-        S2[k] = Tc[k] * st.bg[2];
-        lmax = max(lmax, last[k]);
+        q.S0[k] = q.Tc[k] * st.bg[0];
+        q.S1[k] = q.Tc[k] * st.bg[1];
+        q.S2[k] = q.Tc[k] * st.bg[2];
+        lmax = max(lmax, q.last[k]);
     }
     const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
     uint32_t pos = max(wend, range.x);
@@ -354,55 +417,20 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_backward(BlendArgs a, con
             bits &= bits - 1;
             const float4 *rec = wrec + j * SREC;
             const uint32_t idx = sidx[j];
-            const float4 h0 = rec[0];
-            const int T = __float_as_int(h0.w);
             // per-pixel terms in gradient-record word order, summed over this lane's two pixels
             // (8x8-block coordinates): 3t+0 = g_t x, 3t+1 = g_t y, 3t+2 = g_t, 24 dsigma',
             // 25 dopacity, 26..28 dcolour
             float v32[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v32[q] = 0.f;
-            bool any_on = false;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (idx >= last[k]) continue;
-                PairTerms p;
-                const int code = k ? eval_pair<1>(rec, lx, ly, st, p) : eval_pair<0>(rec, lx, ly, st, p);
-                if (COUNT) count_pair(cnt, rec, code);
-                if (code != 2) continue;
-                any_on = true;
-                const float4 c = rec[1];
-                const float om = 1.0f - p.alpha;
-                const float inv = __frcp_rn(om);
-                const float Tn = Tc[k] * inv;  // transmittance in front of this pair
-                const float dalpha = G0[k] * (Tn * c.x - S0[k] * inv) + G1[k] * (Tn * c.y - S1[k] * inv) +
-                                     G2[k] * (Tn * c.z - S2[k] * inv);
-                const float ta = Tn * p.alpha;
-                v32[G_RGB] += G0[k] * ta;
-                v32[G_RGB + 1] += G1[k] * ta;
-                v32[G_RGB + 2] += G2[k] * ta;
-                S0[k] = fmaf(ta, c.x, S0[k]);
-                S1[k] = fmaf(ta, c.y, S1[k]);
-                S2[k] = fmaf(ta, c.z, S2[k]);
-                Tc[k] = Tn;
-                if (p.oI < st.alpha_max) {
-                    v32[G_OPA] += dalpha * p.I;
-                    const float dI = dalpha * h0.z;
-                    // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
-                    const float dx = -dI * LN2 * p.z * p.I * p.I;
-                    v32[G_SIG] += dx * p.phi2;
-                    const float dphi2 = dx * h0.x * rcp(p.S);
-                    const float ly8 = ly + 4.0f * k;
-#pragma unroll
-                    for (int t = 0; t < KMAX; ++t) {
-                        if (t < T) {
-                            const float gt = dphi2 * p.e[t];
-                            v32[3 * t] = fmaf(gt, lx, v32[3 * t]);
-                            v32[3 * t + 1] = fmaf(gt, ly8, v32[3 * t + 1]);
-                            v32[3 * t + 2] += gt;
-                        }
-                    }
-                }
+            for (int w2 = 0; w2 < 32; ++w2) v32[w2] = 0.f;
+            bool any_on;
+            switch (__float_as_int(rec[0].w)) {  // the record's line count, uniform across the warp
+                case 3: any_on = bwd_record<3, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
+                case 4: any_on = bwd_record<4, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
+                case 5: any_on = bwd_record<5, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
+                case 6: any_on = bwd_record<6, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
+                case 7: any_on = bwd_record<7, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
+                default: any_on = bwd_record<8, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
             }
             if (!__any_sync(0xffffffffu, any_on)) continue;
             // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v32[l]
