@@ -165,10 +165,14 @@ void cs_state_release(cs_fwd_state *state);
 /* Internal arrays of a forward state, copied to host memory for inspection and parity checks.
    which: see cs_array.  host_dst may be NULL to query the size.  Synchronous. */
 typedef enum {
-    CS_ARR_RECORDS = 0,      /* float [R][32]: per (view, convex) screen record, see DESIGN */
+    CS_ARR_RECORDS = 0,      /* float [R][32]: per (view, convex) screen record: anchor vertex (x, y),
+                                d^p sigma, opacity, rgb, packed hull (T | index_i << (4 + 3 i)), then
+                                per hull line t < 8 (A, B, C) = log2(e) d^p delta (n_x, n_y,
+                                n . (anchor - v_t)), i.e. lines relative to the anchor */
     CS_ARR_DEPTH_KEYS = 1,   /* uint32 [R]: binary32 bits of the camera distance; 0xffffffff if not drawn */
     CS_ARR_RECTS = 2,        /* uint32 [R][2]: tile range (tx0 | tx1 << 16, ty0 | ty1 << 16) */
-    CS_ARR_COUNTS = 3,       /* uint32 [R]: number of tiles in the range (0 if not drawn) */
+    CS_ARR_COUNTS = 3,       /* uint32 [R]: number of tiles the convex covers (the whole range, or the
+                                tiles the exact tile test keeps); 0 if not drawn */
     CS_ARR_PAIR_KEYS = 4,    /* uint32 [P]: view << b | tile index within the view, b = bits of the largest
                                 view's tile count (one view: the tile index) */
     CS_ARR_PAIR_VALUES = 5,  /* uint32 [P]: record index (view * N + convex) of each sorted pair */
