@@ -47,10 +47,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2411_14974_gb300.replicas import dist_env as env
+    return env()
 
 
 class ClockSampler:
@@ -455,7 +453,8 @@ def run_ours(args):
         sc = sc.subset(range(args.n))
     cams = cams + syn.sphere_cameras(3, 1920, 1080, 4.0, seed=7)
     # replicas: rank r renders views r, r + N, ... of the cycle (weak scaling, no exchange)
-    cams = [cams[(rank + i * ws) % len(cams)] for i in range(len(cams))]
+    from paper_2411_14974_gb300 import replicas
+    cams = replicas.views_for_rank(cams, rank, ws)
     H, W = cams[0].height, cams[0].width
     scene = cs.SceneTensors.from_numpy(sc, dev)
     dL = torch.as_tensor(np.random.default_rng(1).uniform(-1, 1, (1, 3, H, W)).astype(np.float32), device=dev)
@@ -471,19 +470,10 @@ def run_ours(args):
         st.release()
 
     def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
+        replicas.barrier(dev)
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dev)
 
     for i in range(args.warmup):
         step(i)
@@ -507,7 +497,7 @@ def run_ours(args):
     clk = clocks.stop()
     ms_step = ms_total / args.steps
     pixels_per_step = H * W
-    value = ws * pixels_per_step * args.steps / (ms_total / 1e3) / 1e6
+    value = replicas.job_throughput(pixels_per_step * args.steps, ws, ms_total) / 1e6
 
     # forward-only throughput (same views)
     barrier()
@@ -518,7 +508,7 @@ def run_ours(args):
     f1.record(stream)
     barrier()
     fwd_ms = max_over_ranks(f0.elapsed_time(f1)) / args.steps
-    fwd_mpix = ws * pixels_per_step / (fwd_ms / 1e3) / 1e6
+    fwd_mpix = replicas.job_throughput(pixels_per_step, ws, fwd_ms) / 1e6
 
     breakdown = {k: v[0] / args.steps for k, v in stages.items()}
     out = dict(metric=METRIC, value=value, unit="Mpix/s", n_gpus=ws, steps=args.steps, warmup=args.warmup,
