@@ -438,7 +438,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);
-        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles};
+        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles, s->k};
         CS_TRY(launch_blend_forward(a, stream), "blend");
     }
     for (int v = 0; v < V; ++v) {
@@ -527,7 +527,7 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
-            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles};
+            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k};
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }
@@ -660,7 +660,7 @@ extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, cons
     cudaError_t e = pool_alloc(ctx, (void **)&dc, 12 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 12 * sizeof(unsigned long long), stream);
     const int V = (int)s->views.size();
-    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles};
+    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k};
     if (e == cudaSuccess) e = launch_blend_forward(a, stream, dc);
     if (e == cudaSuccess && dL_dimage && s->n_records) {
         e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);

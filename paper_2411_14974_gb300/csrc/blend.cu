@@ -57,7 +57,7 @@ __device__ __forceinline__ float rcp(float x) {
 // blocks with origins oy and oy + 4).  Returns false when no pixel of the block can pass the
 // line pre-test: for some line, its smallest value over the block's pixel centres exceeds the
 // bound (with a margin for the per-pixel rounding).
-template <int ROWS>
+template <int ROWS, int K>
 __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
                                              float oy, const Settings &st) {
     const float4 *src = records + (size_t)r * (REC_WORDS / 4);
@@ -65,7 +65,7 @@ __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restri
     const int T = (int)hull_pack_count(__float_as_uint(h1.w));
     float L[3 * KMAX];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; q < (3 * K + 3) / 4; ++q) {
         if (4 * q < 3 * T) {
             const float4 v = __ldg(src + 2 + q);
             L[4 * q] = v.x; L[4 * q + 1] = v.y; L[4 * q + 2] = v.z; L[4 * q + 3] = v.w;
@@ -86,7 +86,7 @@ __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restri
     }
     bool pass = true;
 #pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
+    for (int t = 0; t < K; ++t) {
         if (t < T) {
             const float A = L[3 * t], B = L[3 * t + 1], C = L[3 * t + 2];
             const float Cp = fmaf(A, offx, fmaf(B, offy, C));
@@ -95,6 +95,11 @@ __device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restri
             const float margin = (fabsf(Cp) + 8.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
             const float mn = Cp + fminf(0.5f * A, 7.5f * A) + fminf(0.5f * B, ((float)ROWS - 0.5f) * B);
             pass = pass && !(mn > bound + margin);
+        } else {
+            // an unused slot: a line that is -inf everywhere adds 2^-inf = 0 to the sum and never
+            // wins the maximum, so every record is evaluated with K lines
+            const float ninf = -__int_as_float(0x7f800000);
+            dst[3 + t] = make_float4(0.f, 0.f, ninf, ninf);
         }
     }
     dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
@@ -110,9 +115,9 @@ struct PairTerms {
 };
 
 // returns 0 when the line pre-test rejects the pair, 1 when alpha < tau, 2 when it contributes;
-// HALF selects the 8x4 origin (0 upper, 1 lower) the pixel's local coordinates refer to; NT is
-// the record's number of hull lines (the callers branch on it once per record, uniformly across
-// the warp, so the line loops carry no per-line guards)
+// HALF selects the 8x4 origin (0 upper, 1 lower) the pixel's local coordinates refer to; NT = K,
+// the scene's points per convex: every staged record carries K line slots (unused ones are -inf),
+// so the line loops carry no per-line guards
 template <int HALF, int NT>
 __device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float lx, float ly, const Settings &st,
                                          PairTerms &p) {
@@ -221,7 +226,7 @@ __device__ __forceinline__ void tile_of(const ViewDesc &vd, uint32_t g, int &tx,
     ty = (int)(local / (uint32_t)vd.tiles_x);
 }
 
-template <bool COUNT>
+template <bool COUNT, int K>
 __global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[FWD_THREADS / 32][32 * SREC];
     __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
@@ -250,36 +255,51 @@ __global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsi
         const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, range.x, range.y, pos,
                                                 sidx, lane);
         bool pass = false;
-        if (lane < nh) pass = stage_record<4>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
+        if (lane < nh) pass = stage_record<4, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         if (!done) {
+            // two records per iteration: their evaluations are independent (only the compositing
+            // depends on the record in front), which doubles the work between dependent latencies
             while (bits) {
-                const uint32_t j = (uint32_t)(__ffs(bits) - 1);
+                const uint32_t j1 = (uint32_t)(__ffs(bits) - 1);
                 bits &= bits - 1;
-                const float4 *rec = wrec + j * SREC;
-                PairTerms p;
-                int code;
-                switch (__float_as_int(rec[0].w)) {  // the record's line count, uniform across the warp
-                    case 3: code = eval_pair<0, 3>(rec, lx, ly, st, p); break;
-                    case 4: code = eval_pair<0, 4>(rec, lx, ly, st, p); break;
-                    case 5: code = eval_pair<0, 5>(rec, lx, ly, st, p); break;
-                    case 6: code = eval_pair<0, 6>(rec, lx, ly, st, p); break;
-                    case 7: code = eval_pair<0, 7>(rec, lx, ly, st, p); break;
-                    default: code = eval_pair<0, 8>(rec, lx, ly, st, p); break;
+                const uint32_t j2 = bits ? (uint32_t)(__ffs(bits) - 1) : j1;
+                const bool two = bits != 0;
+                bits &= bits - 1;
+                const float4 *rec1 = wrec + j1 * SREC, *rec2 = wrec + j2 * SREC;
+                PairTerms p1, p2;
+                const int code1 = eval_pair<0, K>(rec1, lx, ly, st, p1);
+                const int code2 = two ? eval_pair<0, K>(rec2, lx, ly, st, p2) : 0;
+                if (COUNT) {
+                    count_pair(cnt, rec1, code1);
+                    if (two) count_pair(cnt, rec2, code2);
                 }
-                if (COUNT) count_pair(cnt, rec, code);
-                if (code != 2) continue;
-                const float4 c = rec[1];
-                const float wgt = p.alpha * T;
-                C0 = fmaf(wgt, c.x, C0);
-                C1 = fmaf(wgt, c.y, C1);
-                C2 = fmaf(wgt, c.z, C2);
-                T = T * (1.0f - p.alpha);
-                last = sidx[j] + 1;
-                if (T < st.t_min) {
-                    done = true;
-                    break;
+                if (code1 == 2) {
+                    const float4 c = rec1[1];
+                    const float wgt = p1.alpha * T;
+                    C0 = fmaf(wgt, c.x, C0);
+                    C1 = fmaf(wgt, c.y, C1);
+                    C2 = fmaf(wgt, c.z, C2);
+                    T = T * (1.0f - p1.alpha);
+                    last = sidx[j1] + 1;
+                    if (T < st.t_min) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (code2 == 2) {
+                    const float4 c = rec2[1];
+                    const float wgt = p2.alpha * T;
+                    C0 = fmaf(wgt, c.x, C0);
+                    C1 = fmaf(wgt, c.y, C1);
+                    C2 = fmaf(wgt, c.z, C2);
+                    T = T * (1.0f - p2.alpha);
+                    last = sidx[j2] + 1;
+                    if (T < st.t_min) {
+                        done = true;
+                        break;
+                    }
                 }
             }
         }
@@ -355,7 +375,7 @@ __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint3
     return any_on;
 }
 
-template <bool COUNT>
+template <bool COUNT, int K>
 __global__ void __launch_bounds__(BWD_THREADS, 4) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_blend_backward(BlendArgs a, 
         const int nh = gather_candidates<true>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 7.5f, range.x, range.y, pos,
                                                sidx, lane);
         bool pass = false;
-        if (lane < nh) pass = stage_record<8>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
+        if (lane < nh) pass = stage_record<8, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         while (bits) {  // warp-uniform; slots hold decreasing pair indices
@@ -423,15 +443,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_blend_backward(BlendArgs a, 
             float v32[32];
 #pragma unroll
             for (int w2 = 0; w2 < 32; ++w2) v32[w2] = 0.f;
-            bool any_on;
-            switch (__float_as_int(rec[0].w)) {  // the record's line count, uniform across the warp
-                case 3: any_on = bwd_record<3, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-                case 4: any_on = bwd_record<4, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-                case 5: any_on = bwd_record<5, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-                case 6: any_on = bwd_record<6, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-                case 7: any_on = bwd_record<7, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-                default: any_on = bwd_record<8, COUNT>(rec, idx, lx, ly, st, q, v32, cnt); break;
-            }
+            const bool any_on = bwd_record<K, COUNT>(rec, idx, lx, ly, st, q, v32, cnt);
             if (!__any_sync(0xffffffffu, any_on)) continue;
             // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v32[l]
 #pragma unroll
@@ -464,21 +476,48 @@ __global__ void __launch_bounds__(BWD_THREADS, 4) k_blend_backward(BlendArgs a, 
 
 }  // namespace
 
+template <int K>
+static void blend_forward_k(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
+    if (counts) k_blend_forward<true, K><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
+    else k_blend_forward<false, K><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
+}
+
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (counts) k_blend_forward<true><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
-    else k_blend_forward<false><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
+    switch (a.k) {
+        case 3: blend_forward_k<3>(a, s, counts); break;
+        case 4: blend_forward_k<4>(a, s, counts); break;
+        case 5: blend_forward_k<5>(a, s, counts); break;
+        case 6: blend_forward_k<6>(a, s, counts); break;
+        case 7: blend_forward_k<7>(a, s, counts); break;
+        case 8: blend_forward_k<8>(a, s, counts); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int K>
+static void blend_backward_k(const BlendArgs &a, const float *dL_dimage, int64_t image_stride, float4 *grad_records,
+                             cudaStream_t s, unsigned long long *counts) {
+    if (counts)
+        k_blend_backward<true, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
+    else
+        k_blend_backward<false, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
 }
 
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,
                                   float4 *grad_records, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
-    if (counts)
-        k_blend_backward<true><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
-    else
-        k_blend_backward<false><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
+    switch (a.k) {
+        case 3: blend_backward_k<3>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        case 4: blend_backward_k<4>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        case 5: blend_backward_k<5>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        case 6: blend_backward_k<6>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        case 7: blend_backward_k<7>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        case 8: blend_backward_k<8>(a, dL_dimage, image_stride, grad_records, s, counts); break;
+        default: return cudaErrorInvalidValue;
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -114,6 +114,7 @@ struct BlendArgs {
     const float4 *bboxes;
     Settings st;
     uint32_t n_tiles;
+    int k;  // points per convex: at most k hull lines per record
 };
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);

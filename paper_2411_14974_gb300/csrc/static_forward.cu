@@ -150,7 +150,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const uint32_t *vals = in_b ? pv2 : pv;
     if (e == cudaSuccess) e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, ranges, tiles, stream);
     if (e == cudaSuccess) {
-        BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles};
+        BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles, scene->k};
         e = launch_blend_forward(a, stream);
     }
     if (e != cudaSuccess) return fail_cuda(e, "cs_forward_static");
