@@ -549,6 +549,28 @@ def run_ours(args):
                                work_per_launch=tot,
                                traffic=_profiled_traffic(f"k_blend_{'forward' if dom == 'blend' else 'backward'}"),
                                traffic_unit="bytes per launch (ncu dram read + write)")
+        # every stage against its own bound: the preprocess kernels against the measured HBM copy
+        # rate with their algorithmic bytes (scene read, record and keys written; the backward
+        # also reads both 128-byte records and updates the gradients in place), the blends
+        # against the MUFU and FP32 issue rates with the work counted above
+        hbm = _hbm_peak()
+        n_conv = sc.n
+        sh_w = 3 * (sc.sh_degree + 1) ** 2
+        p_bytes = 4 * (sc.k * 3 + 3 + sh_w)
+        pre_bytes = n_conv * (p_bytes + 128 + 4 + 4 + 8 + 16 + 4)
+        # backward: parameters, the record's first 32 bytes (hull), the 128-byte gradient record,
+        # points and SH gradients read and written back, delta / sigma / opacity gradients likewise
+        bwd_bytes = n_conv * (p_bytes + 32 + 128 + 2 * 4 * (sc.k * 3 + sh_w) + 3 * 4 * 2)
+        stages = {}
+        stages["preprocess"] = dict(bound="hbm", bytes=pre_bytes, achieved_gbs=pre_bytes / (breakdown["preprocess"] / 1e3) / 1e9,
+                                    peak_gbs=hbm)
+        stages["preprocess_backward"] = dict(bound="hbm", bytes=bwd_bytes,
+                                             achieved_gbs=bwd_bytes / (breakdown["preprocess_backward"] / 1e3) / 1e9,
+                                             peak_gbs=hbm)
+        for st_name in ("preprocess", "preprocess_backward"):
+            stages[st_name]["frac"] = stages[st_name]["achieved_gbs"] / hbm
+        stages[dom] = dict(bound="alu", mufu_frac=achieved / mufu_peak, fp32_frac=fp32 / t / 1e9 / fp32_peak)
+        out["roofline_stages"] = stages
         # end to end through the host-buffer C-ABI call: scene and cotangent uploaded, image and
         # gradients read back, every step
         pin = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory()

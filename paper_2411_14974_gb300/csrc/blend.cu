@@ -227,7 +227,7 @@ __device__ __forceinline__ void tile_of(const ViewDesc &vd, uint32_t g, int &tx,
 }
 
 template <bool COUNT, int K>
-__global__ void __launch_bounds__(FWD_THREADS) k_blend_forward(BlendArgs a, unsigned long long *counts) {
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[FWD_THREADS / 32][32 * SREC];
     __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
     const uint32_t g = blockIdx.x;
