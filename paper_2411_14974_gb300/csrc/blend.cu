@@ -327,17 +327,49 @@ struct BwdPixels {
 // Undoes record rec (pair index idx, NT lines) for both pixels of the lane: recovers T in front
 // of the pair, accumulates the per-pixel gradient terms into v32, and returns whether any of the
 // two pixels received a contribution.
+// The rest of eval_pair once the line values s[] of one pixel are known.
+template <int NT>
+__device__ __forceinline__ int eval_from_lines(const float (&s)[NT], float m, const float4 &h0, const Settings &st,
+                                               PairTerms &p) {
+    if (m > h0.y) return 0;
+    float S = 0.f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        p.e[t] = ex2(s[t] - m);
+        S += p.e[t];
+    }
+    p.S = S;
+    p.phi2 = m + lg2(S);
+    p.z = ex2(h0.x * p.phi2);
+    p.I = rcp(1.0f + p.z);
+    p.oI = h0.z * p.I;
+    p.alpha = fminf(st.alpha_max, p.oI);
+    return p.alpha >= st.tau ? 2 : 1;
+}
+
 template <int NT, bool COUNT>
 __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint32_t idx, float lx, float ly,
                                            const Settings &st, BwdPixels &q, float (&v32)[32],
                                            unsigned long long (&cnt)[NCOUNT]) {
     const float4 h0 = rec[0];
     bool any_on = false;
+    // line values of both pixels from one read of each staged line (the lower pixel's block origin
+    // is the record's second C)
+    float sv[2][NT];
+    float mv[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const float4 L = rec[3 + t];
+        sv[0][t] = fmaf(L.x, lx, fmaf(L.y, ly, L.z));
+        sv[1][t] = fmaf(L.x, lx, fmaf(L.y, ly, L.w));
+        mv[0] = fmaxf(mv[0], sv[0][t]);
+        mv[1] = fmaxf(mv[1], sv[1][t]);
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         if (idx >= q.last[k]) continue;
         PairTerms p;
-        const int code = k ? eval_pair<1, NT>(rec, lx, ly, st, p) : eval_pair<0, NT>(rec, lx, ly, st, p);
+        const int code = eval_from_lines<NT>(sv[k], mv[k], h0, st, p);
         if (COUNT) count_pair(cnt, rec, code);
         if (code != 2) continue;
         any_on = true;
