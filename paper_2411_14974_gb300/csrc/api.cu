@@ -321,6 +321,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     unsigned long long *scan_tmp = nullptr, *total = nullptr;
     float *radii = nullptr;
     uint64_t P = 0;
+    uint32_t key_min = 0;
+    int depth_bits = 0;
     bool in_b = false;
     uint32_t max_view_tiles = 1;
     for (int v = 0; v < V; ++v) {
@@ -358,10 +360,28 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     }
     CS_TRY(cudaMemcpyAsync(s->views_dev, s->views.data(), sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, stream),
            "copy views");
+    CS_TRY(pool_alloc(ctx, (void **)&total, sizeof(PreprocessStats), stream), "alloc");
+    CS_TRY(cudaMemsetAsync(total, 0, sizeof(PreprocessStats), stream), "clear totals");
     {
         StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
-        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes, radii};
+        PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes, radii,
+                         reinterpret_cast<PreprocessStats *>(total)};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
+    }
+    // the forward's one host synchronisation: the pair count (to size the pair lists) and the range
+    // of the drawn records' depth keys (the depth sort orders only the bits in which they differ)
+    CS_TRY(cudaMemcpyAsync(ctx->host_total, total, sizeof(PreprocessStats), cudaMemcpyDeviceToHost, stream),
+           "read totals");
+    CS_TRY(cudaStreamSynchronize(stream), "synchronize");
+    {
+        const PreprocessStats tot = *reinterpret_cast<const PreprocessStats *>(ctx->host_total);
+        P = tot.pairs;
+        if (P >= 0xffffffffull) {
+            st_code = fail(CS_ERR_ARG, "%llu tile pairs exceed the 32-bit pair index", (unsigned long long)P);
+            goto cleanup;
+        }
+        key_min = ~tot.key_min_inv;
+        depth_bits = P ? bits_for((uint64_t)(tot.key_max - key_min) + 1) : 0;
     }
     // depth order of the records
     {
@@ -373,16 +393,11 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&offsets, (size_t)R * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words(R) * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_words * 8, stream), "alloc");
-        CS_TRY(pool_alloc(ctx, (void **)&total, 16, stream), "alloc");
         {
             StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
-            if (R > 0) {
-                CS_TRY(cudaMemcpyAsync(sort_keys_a, s->depth_keys, (size_t)R * 4, cudaMemcpyDeviceToDevice, stream),
-                       "copy keys");
-            }
-            CS_TRY(launch_iota(sort_vals_a, R, stream), "iota");
-            CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, 32, radix_tmp, scan_tmp,
-                                    &in_b, stream),
+            CS_TRY(launch_depth_sort_input(s->depth_keys, R, key_min, sort_keys_a, sort_vals_a, stream), "sort input");
+            CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
+                                    scan_tmp, &in_b, stream),
                    "depth sort");
         }
         uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;
@@ -397,14 +412,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             if (vb) sorted = vv2;
         }
         StageTimer tm(ctx, CS_STAGE_SCAN_EMIT, stream);
-        CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, total, scan_tmp, stream), "scan");
-        CS_TRY(cudaMemcpyAsync(ctx->host_total, total, 8, cudaMemcpyDeviceToHost, stream), "read pair count");
-        CS_TRY(cudaStreamSynchronize(stream), "synchronize");
-        P = ctx->host_total[0];
-        if (P >= 0xffffffffull) {
-            st_code = fail(CS_ERR_ARG, "%llu tile pairs exceed the 32-bit pair index", (unsigned long long)P);
-            goto cleanup;
-        }
+        CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, nullptr, scan_tmp, stream), "scan");
         s->n_pairs = (int64_t)P;
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_keys, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");

@@ -61,6 +61,14 @@ __host__ __device__ inline uint32_t hull_pack_count(uint32_t packed) { return pa
 __host__ __device__ inline int hull_pack_index(uint32_t packed, int i) { return (int)((packed >> (4 + 3 * i)) & 7u); }
 
 // ---- launch wrappers implemented in the .cu files --------------------------------------------
+// totals of a preprocess launch, accumulated with atomics into a zeroed struct: the pairs to emit
+// and the range of the drawn records' depth keys (the minimum kept as the maximum of its complement
+// so that all-zero bytes are the empty state)
+struct PreprocessStats {
+    unsigned long long pairs;
+    unsigned int key_max, key_min_inv;
+};
+
 struct PreprocessOut {
     float4 *records;       // [R][8]
     uint32_t *depth_keys;  // [R]
@@ -68,6 +76,7 @@ struct PreprocessOut {
     uint32_t *counts;      // [R]
     float4 *bboxes;        // [R] pixel box (xmin, ymin, xmax, ymax) holding every pixel with alpha >= tau
     float *radii;          // [R] kappa r, the tile test's bound in record units
+    PreprocessStats *stats;  // zeroed before the launch
 };
 cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n,
                               int k, const Settings &st, const PreprocessOut &out, cudaStream_t s);
@@ -93,7 +102,11 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
                              cudaStream_t s);
 
-cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s);
+// the depth sort's input: keys_out[i] = depth_keys[i] - key_min (mod 2^32), vals_out[i] = i.  The
+// drawn records' keys then lie in [0, key_max - key_min]; undrawn records (which emit no pairs)
+// take whatever low bits the subtraction leaves them
+cudaError_t launch_depth_sort_input(const uint32_t *depth_keys, int64_t n, uint32_t key_min, uint32_t *keys_out,
+                                    uint32_t *vals_out, cudaStream_t s);
 // keys[j] = view index of record sorted_records[j]
 cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
                              uint32_t *keys, cudaStream_t s);

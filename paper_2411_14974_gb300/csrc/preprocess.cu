@@ -296,6 +296,32 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
         out.counts[rec] = drawn ? count : 0u;
         out.rects[rec] = drawn ? rect : make_uint2(0, 0);
     }
+    // the launch's pair total and depth-key range: one set of atomics per block
+    __shared__ uint32_t bsum[PRE_THREADS / 32], bmax[PRE_THREADS / 32], bmin_inv[PRE_THREADS / 32];
+    const uint32_t wsum = __reduce_add_sync(0xffffffffu, drawn ? count : 0u);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, drawn ? depth_key : 0u);
+    const uint32_t wmin_inv = __reduce_max_sync(0xffffffffu, drawn ? ~depth_key : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        bsum[threadIdx.x >> 5] = wsum;
+        bmax[threadIdx.x >> 5] = wmax;
+        bmin_inv[threadIdx.x >> 5] = wmin_inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        uint32_t mx = 0, mi = 0;
+#pragma unroll
+        for (int q = 0; q < PRE_THREADS / 32; ++q) {
+            s += bsum[q];
+            mx = max(mx, bmax[q]);
+            mi = max(mi, bmin_inv[q]);
+        }
+        if (s) {
+            atomicAdd(&out.stats->pairs, s);
+            atomicMax(&out.stats->key_max, mx);
+            atomicMax(&out.stats->key_min_inv, mi);
+        }
+    }
 }
 
 }  // namespace

@@ -237,9 +237,13 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
 }
 
 // ---- pairs ----------------------------------------------------------------------------------
-__global__ void k_iota(uint32_t *v, int64_t n) {
+__global__ void k_depth_sort_input(const uint32_t *__restrict__ depth_keys, int64_t n, uint32_t key_min,
+                                   uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = (uint32_t)i;
+    if (i < n) {
+        keys_out[i] = depth_keys[i] - key_min;
+        vals_out[i] = (uint32_t)i;
+    }
 }
 
 __device__ __forceinline__ int view_of_record(const ViewDesc *__restrict__ views, int n_views, uint32_t r) {
@@ -402,9 +406,10 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
     return cudaGetLastError();
 }
 
-cudaError_t launch_iota(uint32_t *v, int64_t n, cudaStream_t s) {
+cudaError_t launch_depth_sort_input(const uint32_t *depth_keys, int64_t n, uint32_t key_min, uint32_t *keys_out,
+                                    uint32_t *vals_out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_iota<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n);
+    k_depth_sort_input<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(depth_keys, n, key_min, keys_out, vals_out);
     count_launches(1);
     return cudaGetLastError();
 }

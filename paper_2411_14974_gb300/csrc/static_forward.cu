@@ -43,7 +43,7 @@ struct Carve {
     }
 };
 
-int bits_for_tiles(uint64_t n) {
+int bits_for(uint64_t n) {
     int b = 0;
     while (b < 32 && ((uint64_t)1 << b) < n) ++b;
     return b;
@@ -117,7 +117,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const int64_t max_sort = CS_STATIC_MAX_PAIRS > CS_STATIC_MAX_CONVEXES ? CS_STATIC_MAX_PAIRS : CS_STATIC_MAX_CONVEXES;
     uint32_t *radix_tmp = c.take<uint32_t>(radix_tmp_words(max_sort));
     unsigned long long *scan_tmp = c.take<unsigned long long>(scan_tmp_words(max_sort) + scan_tmp_words(256 * (max_sort / 4096 + 2)));
-    unsigned long long *total = c.take<unsigned long long>(1);
+    PreprocessStats *totals = c.take<PreprocessStats>(1);
     uint2 *ranges = c.take<uint2>(tiles);
     uint32_t *n_last = c.take<uint32_t>(pixels);
     if (c.used > STATIC_BYTES) return fail(CS_ERR_BUDGET, "cs_forward_static: %dx%d needs more than the static array",
@@ -125,24 +125,28 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     vd.n_last = n_last;
 
     e = cudaMemcpyAsync(views_dev, &vd, sizeof vd, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(totals, 0, sizeof(PreprocessStats), stream);
     if (e == cudaSuccess) {
-        PreprocessOut po{records, depth_keys, rects, counts, bboxes, radii};
+        PreprocessOut po{records, depth_keys, rects, counts, bboxes, radii, totals};
         e = launch_preprocess(views_dev, &vd, 1, R, scene->k, s, po, stream);
     }
-    bool in_b = false;
-    if (e == cudaSuccess && R > 0) e = cudaMemcpyAsync(ka, depth_keys, (size_t)R * 4, cudaMemcpyDeviceToDevice, stream);
-    if (e == cudaSuccess) e = launch_iota(va, R, stream);
-    if (e == cudaSuccess) e = radix_sort_pairs(ka, va, kb, vb, R, 32, radix_tmp, scan_tmp, &in_b, stream);
-    const uint32_t *sorted = in_b ? vb : va;
-    if (e == cudaSuccess) e = launch_exclusive_scan(counts, sorted, offsets, R, total, scan_tmp, stream);
-    unsigned long long P = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&P, total, sizeof P, cudaMemcpyDeviceToHost, stream);
+    // one host synchronisation: the pair count and the drawn records' depth-key range
+    PreprocessStats tot{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, totals, sizeof tot, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return fail_cuda(e, "cs_forward_static");
+    const unsigned long long P = tot.pairs;
     if (P > (unsigned long long)CS_STATIC_MAX_PAIRS)
         return fail(CS_ERR_BUDGET, "cs_forward_static: %llu tile pairs exceed the static limit of %d", P,
                     CS_STATIC_MAX_PAIRS);
-    const int local_bits = bits_for_tiles(tiles);
+    const uint32_t key_min = ~tot.key_min_inv;
+    const int depth_bits = P ? bits_for((uint64_t)(tot.key_max - key_min) + 1) : 0;
+    bool in_b = false;
+    e = launch_depth_sort_input(depth_keys, R, key_min, ka, va, stream);
+    if (e == cudaSuccess) e = radix_sort_pairs(ka, va, kb, vb, R, depth_bits, radix_tmp, scan_tmp, &in_b, stream);
+    const uint32_t *sorted = in_b ? vb : va;
+    if (e == cudaSuccess) e = launch_exclusive_scan(counts, sorted, offsets, R, nullptr, scan_tmp, stream);
+    const int local_bits = bits_for(tiles);
     e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, R, local_bits, pk, pv, stream);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);
