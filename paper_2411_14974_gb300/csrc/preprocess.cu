@@ -20,37 +20,24 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
     const int64_t n = vd.n;
     const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     if (i0 >= n) return;  // whole block
-    __shared__ float sp[PRE_THREADS * K * 3];
-    __shared__ __align__(16) float ssh[PRE_THREADS * SH_MAX_WORDS];
+    constexpr int PS = (3 * K) | 1;  // odd stride of a convex's staged points: no bank conflicts
+    __shared__ float sp[PRE_THREADS * PS];
+    __shared__ __align__(16) float ssh[PRE_THREADS * SH_STAGE_WORDS];
     __shared__ float scoop[PRE_THREADS / 32][3 * KMAX + 3];
     const int cnt = (int)min((int64_t)PRE_THREADS, n - i0);
     const int shw = 3 * (vd.sh_degree + 1) * (vd.sh_degree + 1);
-    constexpr int esz = STG == CS_STORE_F32 ? 4 : 2;
     // The block's SH coefficients (the bulk of its input bytes, needed last) are copied into
     // shared memory asynchronously, in their stored format, while the projection and hull run.
-    {
-        const char *src = reinterpret_cast<const char *>(vd.sh) + (size_t)i0 * shw * esz;
-        char *dst = reinterpret_cast<char *>(ssh);
-        const int bytes = cnt * shw * esz;
-        const int n16 = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) ? bytes / 16 : 0;
-        for (int q = threadIdx.x; q < n16; q += PRE_THREADS) cp_async_16(dst + 16 * q, src + 16 * q);
-        if (STG == CS_STORE_F32) {
-            for (int q = 4 * n16 + threadIdx.x; q < bytes / 4; q += PRE_THREADS) cp_async_4(dst + 4 * q, src + 4 * q);
-        } else {  // 16-bit tail (or a 2-byte aligned array): plain copies, ordered by the barrier below
-            const uint16_t *s16 = reinterpret_cast<const uint16_t *>(src);
-            uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
-            for (int q = 8 * n16 + threadIdx.x; q < bytes / 2; q += PRE_THREADS) d16[q] = __ldg(s16 + q);
-        }
-        cp_async_commit();
-    }
+    const int sh_stride = stage_sh<STG>(ssh, vd.sh, i0, cnt, shw);
     {
         const int words = cnt * K * 3;
-        for (int j = threadIdx.x; j < words; j += PRE_THREADS) sp[j] = ld_param<STG>(vd.points, i0 * K * 3 + j);
+        for (int j = threadIdx.x; j < words; j += PRE_THREADS)
+            sp[(j / (3 * K)) * PS + j % (3 * K)] = ld_param<STG>(vd.points, i0 * K * 3 + j);
     }
     __syncthreads();
     const int64_t i = i0 + threadIdx.x;
     const int64_t rec = vd.rec_base + i;
-    const float *P = sp + threadIdx.x * K * 3;
+    const float *P = sp + threadIdx.x * PS;
 
     uint32_t depth_key = 0xffffffffu, count = 0;
     uint2 rect = make_uint2(0, 0);
@@ -269,22 +256,12 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
         const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
         const float il = rsqrtf(wx * wx + wy * wy + wz * wz);
         const float dx = wx * il, dy = wy * il, dz = wz * il;
-        const int sb = threadIdx.x * shw;
         const int nb = (vd.sh_degree + 1) * (vd.sh_degree + 1);
-        float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {  // basis streamed term by term (j is a constant per term)
-            if (j < nb) {
-                float gx, gy, gz;
-                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
-                raw0 += sm_param<STG>(ssh, sb + 3 * j) * Yj;
-                raw1 += sm_param<STG>(ssh, sb + 3 * j + 1) * Yj;
-                raw2 += sm_param<STG>(ssh, sb + 3 * j + 2) * Yj;
-            }
-        }
-        w[R_RGB + 0] = fmaxf(raw0, 0.f);
-        w[R_RGB + 1] = fmaxf(raw1, 0.f);
-        w[R_RGB + 2] = fmaxf(raw2, 0.f);
+        float raw[3];
+        sh_colour<STG>(ssh, threadIdx.x, shw, sh_stride, nb, dx, dy, dz, raw);
+        w[R_RGB + 0] = fmaxf(raw[0], 0.f);
+        w[R_RGB + 1] = fmaxf(raw[1], 0.f);
+        w[R_RGB + 2] = fmaxf(raw[2], 0.f);
         float4 *dst = out.records + rec * (REC_WORDS / 4);
 #pragma unroll
         for (int q = 0; q < REC_WORDS / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);

@@ -8,9 +8,12 @@
 namespace cs {
 namespace {
 
-// Backward: one thread per drawn convex.  With one view, the points and SH gradients of the
-// block's convexes are accumulated (+=) in shared memory and read / written back with coalesced
-// accesses; with several views, convexes are shared between views and use global atomics.
+// Backward: one thread per drawn convex.  The block's SH coefficients are staged in shared memory
+// (coalesced asynchronous copy, conflict-free layout).  With one view, the points and SH gradients
+// of the block's convexes are gathered in shared memory and added to the outputs with coalesced
+// accesses (binary32 SH: each thread overwrites its own staged coefficients with their gradients
+// once it has read them); with several views, convexes are shared between views and use global
+// atomics.
 template <int K, int DEG, bool ATOMIC, int STG>
 __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const ViewDesc *__restrict__ views, Settings st,
                                                                      const float4 *__restrict__ records,
@@ -20,22 +23,42 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const Vi
     constexpr int NB = (DEG + 1) * (DEG + 1);
     constexpr int PW = K * 3, SW = NB * 3;           // words per convex
     constexpr int PS = PW | 1, SS = SW | 1;          // odd strides: no bank conflicts
+    constexpr int esz = STG == CS_STORE_F32 ? 4 : 2;
+    constexpr bool CHUNKED = (SW * esz) % 16 == 0;   // degrees 1 and 3: 16-byte chunk layout possible
+    constexpr bool IN_PLACE = !ATOMIC && STG == CS_STORE_F32;  // SH gradients overwrite the staged SH
+    constexpr bool SEP_DSH = !ATOMIC && STG != CS_STORE_F32;   // 16-bit SH: a separate binary32 buffer
     __shared__ float s_dp[ATOMIC ? 1 : PRE_THREADS * PS];
-    __shared__ float s_dsh[ATOMIC ? 1 : PRE_THREADS * SS];
+    __shared__ __align__(16) float ssh[PRE_THREADS * (STG == CS_STORE_F32 ? SH_STAGE_WORDS : SH_STAGE_WORDS / 2 + 2)];
+    __shared__ float s_dsh[SEP_DSH ? PRE_THREADS * SS : 1];
     const ViewDesc &vd = views[blockIdx.y];
     const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
     if (i0 >= vd.n) return;
     const int cnt = (int)min((int64_t)PRE_THREADS, vd.n - i0);
+    const int sh_stride = stage_sh<STG>(ssh, vd.sh, i0, cnt, SW);
     if (!ATOMIC) {
         if (out.dpoints)
             for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) s_dp[(q / PW) * PS + q % PW] = out.dpoints[i0 * PW + q];
-        if (out.dsh)
+        if (SEP_DSH && out.dsh)
             for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) s_dsh[(q / SW) * SS + q % SW] = out.dsh[i0 * SW + q];
-        __syncthreads();
     }
+    // slot of SH word w of this thread's convex in the staged buffer (binary32 words)
+    auto sh_slot = [&](int w) -> float & {
+        float *base = ssh + (sh_stride ? threadIdx.x * sh_stride * 4 : threadIdx.x * SW);
+        return base[w];
+    };
+    auto zero_sh_slots = [&]() {
+        if (IN_PLACE) {
+#pragma unroll
+            for (int w = 0; w < SW; ++w) sh_slot(w) = 0.f;
+        }
+    };
     const int64_t i = i0 + threadIdx.x;
     const int64_t rec = vd.rec_base + i;
-    if (i < vd.n && counts[rec] != 0) {
+    const bool live = i < vd.n && counts[rec] != 0;
+    cp_async_wait_all();
+    __syncthreads();  // staged SH (and, with one view, the gathered gradients) visible to the block
+    if (!live && i < vd.n) zero_sh_slots();
+    if (live) {
         float gw[GRAD_WORDS];
         const float4 h0 = records[rec * (REC_WORDS / 4)], h1 = records[rec * (REC_WORDS / 4) + 1];
 #pragma unroll
@@ -44,6 +67,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const Vi
             gw[4 * q] = b.x; gw[4 * q + 1] = b.y; gw[4 * q + 2] = b.z; gw[4 * q + 3] = b.w;
         }
         (void)h0;
+        static_assert(R_RGB == 4 && R_HULL == 7, "colour and hull in the record's second float4");
         const uint32_t hull = __float_as_uint(h1.w);
         const int T = (int)hull_pack_count(hull);
         float delta = ld_param<STG>(vd.delta, i), sigma = ld_param<STG>(vd.sigma, i);
@@ -159,46 +183,72 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const Vi
             const float wx = c[0] - vd.campos[0], wy = c[1] - vd.campos[1], wz = c[2] - vd.campos[2];
             const float iwl = rsqrtf(wx * wx + wy * wy + wz * wz);
             const float dx = wx * iwl, dy = wy * iwl, dz = wz * iwl;
-            const int64_t shb = i * SW;
-            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
-#pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                float gx, gy, gz;
-                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
-                raw0 += ld_param<STG>(vd.sh, shb + 3 * j) * Yj;
-                raw1 += ld_param<STG>(vd.sh, shb + 3 * j + 1) * Yj;
-                raw2 += ld_param<STG>(vd.sh, shb + 3 * j + 2) * Yj;
-            }
-            const float gr0 = raw0 > 0.f ? gw[G_RGB] : 0.f;
-            const float gr1 = raw1 > 0.f ? gw[G_RGB + 1] : 0.f;
-            const float gr2 = raw2 > 0.f ? gw[G_RGB + 2] : 0.f;
+            // the record holds max(raw, 0) per channel, so it is positive exactly where the clamp
+            // passes the gradient
+            const float gr[3] = {h1.x > 0.f ? gw[G_RGB] : 0.f, h1.y > 0.f ? gw[G_RGB + 1] : 0.f,
+                                 h1.z > 0.f ? gw[G_RGB + 2] : 0.f};
             float ddx = 0.f, ddy = 0.f, ddz = 0.f;
-            if (gr0 != 0.f || gr1 != 0.f || gr2 != 0.f) {
+            // dL/dc_jc = Y_j gr_c; the direction gradient sums (sum_c c_jc gr_c) dY_j/dd
+            auto emit = [&](int j, int c, float d) {
+                if (ATOMIC) {
+                    if (out.dsh && d != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + c, d);
+                } else if (SEP_DSH) {
+                    s_dsh[threadIdx.x * SS + 3 * j + c] += d;
+                }
+            };
+            if (gr[0] != 0.f || gr[1] != 0.f || gr[2] != 0.f) {
+                if (CHUNKED && sh_stride) {
+                    constexpr int EPC = 16 / esz;  // elements per chunk
+                    uint4 *s4 = reinterpret_cast<uint4 *>(ssh) + threadIdx.x * sh_stride;
+                    uint4 ch = make_uint4(0u, 0u, 0u, 0u);
+                    float dch[4];
 #pragma unroll
-                for (int j = 0; j < NB; ++j) {
-                    float gx, gy, gz;
-                    const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
-                    const float d0 = Yj * gr0, d1 = Yj * gr1, d2 = Yj * gr2;
-                    if (ATOMIC) {
-                        if (out.dsh) {
-                            if (d0 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j, d0);
-                            if (d1 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 1, d1);
-                            if (d2 != 0.f) atomicAdd(out.dsh + i * SW + 3 * j + 2, d2);
+                    for (int j = 0; j < NB; ++j) {
+                        float gx, gy, gz;
+                        const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                        float sg = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const int w = 3 * j + c;
+                            if (w % EPC == 0) ch = s4[w / EPC];
+                            sg += chunk_elem<STG>(ch, w % EPC) * gr[c];
+                            const float d = Yj * gr[c];
+                            emit(j, c, d);
+                            if (IN_PLACE) {  // the chunk's four words are read before it is overwritten
+                                dch[w % 4] = d;
+                                if (w % 4 == 3) s4[w / 4] = make_uint4(__float_as_uint(dch[0]), __float_as_uint(dch[1]),
+                                                                       __float_as_uint(dch[2]), __float_as_uint(dch[3]));
+                            }
                         }
-                    } else {
-                        s_dsh[threadIdx.x * SS + 3 * j] += d0;
-                        s_dsh[threadIdx.x * SS + 3 * j + 1] += d1;
-                        s_dsh[threadIdx.x * SS + 3 * j + 2] += d2;
+                        if (DEG > 0) {
+                            ddx += sg * gx;
+                            ddy += sg * gy;
+                            ddz += sg * gz;
+                        }
                     }
-                    if (DEG > 0) {
-                        const float sg = ld_param<STG>(vd.sh, shb + 3 * j) * gr0 +
-                                         ld_param<STG>(vd.sh, shb + 3 * j + 1) * gr1 +
-                                         ld_param<STG>(vd.sh, shb + 3 * j + 2) * gr2;
-                        ddx += sg * gx;
-                        ddy += sg * gy;
-                        ddz += sg * gz;
+                } else {
+                    const int sb = threadIdx.x * SW;
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        float gx, gy, gz;
+                        const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+                        float sg = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            sg += sm_param<STG>(ssh, sb + 3 * j + c) * gr[c];
+                            const float d = Yj * gr[c];
+                            emit(j, c, d);
+                            if (IN_PLACE) ssh[sb + 3 * j + c] = d;
+                        }
+                        if (DEG > 0) {
+                            ddx += sg * gx;
+                            ddy += sg * gy;
+                            ddz += sg * gz;
+                        }
                     }
                 }
+            } else {
+                zero_sh_slots();
             }
             const float dd = dx * ddx + dy * ddy + dz * ddz;
             dc[0] += (ddx - dx * dd) * iwl;
@@ -226,8 +276,18 @@ __global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const Vi
         __syncthreads();
         if (out.dpoints)
             for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) out.dpoints[i0 * PW + q] = s_dp[(q / PW) * PS + q % PW];
-        if (out.dsh)
-            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) out.dsh[i0 * SW + q] = s_dsh[(q / SW) * SS + q % SW];
+        if (out.dsh) {
+            if (IN_PLACE) {
+                for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) {
+                    const int t = q / SW;
+                    const float d = sh_stride ? ssh[t * sh_stride * 4 + (q - t * SW)] : ssh[q];
+                    out.dsh[i0 * SW + q] += d;
+                }
+            } else {
+                for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS)
+                    out.dsh[i0 * SW + q] = s_dsh[(q / SW) * SS + q % SW];
+            }
+        }
     }
 }
 

@@ -232,5 +232,97 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int SH_MAX_WORDS = 48;  // 3 x (3 + 1)^2
 
+// ---- a block's SH coefficients staged in shared memory ----------------------------------------
+// Convex t of the block starts at 16-byte chunk t * stride, the stride being its chunk count
+// rounded up to an odd number, so that the 16-byte loads of 8 consecutive threads fall in 8
+// distinct groups of 4 banks.  When a convex's coefficients are not a whole number of chunks
+// (degrees 0 and 2) or the array is not 16-byte aligned, they are staged element by element at a
+// stride of shw elements (stride 0 below), odd for degrees 0 and 2.
+constexpr int SH_STAGE_WORDS = 52;  // 32-bit words per convex: 13 chunks (degree 3, binary32)
+
+__host__ __device__ inline int sh_chunk_stride(int shw, int esz) {
+    const int b = shw * esz;
+    return (b % 16) ? 0 : ((b / 16) | 1);
+}
+
+// element e (a compile-time constant after unrolling) of a 16-byte chunk of STG values, widened
+template <int STG>
+__device__ __forceinline__ float chunk_elem(const uint4 &c, int e) {
+    if (STG == CS_STORE_F32) return __uint_as_float(e == 0 ? c.x : e == 1 ? c.y : e == 2 ? c.z : c.w);
+    const int q = e >> 1;
+    const uint32_t u = q == 0 ? c.x : q == 1 ? c.y : q == 2 ? c.z : c.w;
+    const uint16_t b = (e & 1) ? (uint16_t)(u >> 16) : (uint16_t)(u & 0xffffu);
+    return STG == CS_STORE_F16 ? __half2float(__ushort_as_half(b)) : __uint_as_float((uint32_t)b << 16);
+}
+
+// Issues the asynchronous copy of the block's SH coefficients (cnt convexes from i0) into ssh
+// (PRE_THREADS * SH_STAGE_WORDS words) and returns the layout's chunk stride (0: element layout).
+// The caller waits with cp_async_wait_all() and a block barrier before reading.
+template <int STG>
+__device__ __forceinline__ int stage_sh(void *ssh, const void *sh, int64_t i0, int cnt, int shw) {
+    constexpr int esz = STG == CS_STORE_F32 ? 4 : 2;
+    const char *src = reinterpret_cast<const char *>(sh) + (size_t)i0 * shw * esz;
+    char *dst = reinterpret_cast<char *>(ssh);
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    const int stride = aligned ? sh_chunk_stride(shw, esz) : 0;
+    if (stride) {
+        const int cpc = shw * esz / 16, n = cnt * cpc;
+        for (int q = threadIdx.x; q < n; q += PRE_THREADS) {
+            const int t = q / cpc;
+            cp_async_16(dst + 16 * (t * stride + q - t * cpc), src + 16 * q);
+        }
+    } else {
+        const int bytes = cnt * shw * esz;
+        const int n16 = aligned ? bytes / 16 : 0;
+        for (int q = threadIdx.x; q < n16; q += PRE_THREADS) cp_async_16(dst + 16 * q, src + 16 * q);
+        if (STG == CS_STORE_F32) {
+            for (int q = 4 * n16 + threadIdx.x; q < bytes / 4; q += PRE_THREADS) cp_async_4(dst + 4 * q, src + 4 * q);
+        } else {  // 16-bit tail (or a 2-byte aligned array): plain copies, ordered by the caller's barrier
+            const uint16_t *s16 = reinterpret_cast<const uint16_t *>(src);
+            uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
+            for (int q = 8 * n16 + threadIdx.x; q < bytes / 2; q += PRE_THREADS) d16[q] = __ldg(s16 + q);
+        }
+    }
+    cp_async_commit();
+    return stride;
+}
+
+// Raw colour 0.5 + sum_j c_j Y_j(d) of staged convex t (nb = (degree + 1)^2 basis functions),
+// accumulated term by term in basis order.
+template <int STG>
+__device__ __forceinline__ void sh_colour(const void *ssh, int t, int shw, int stride, int nb, float dx, float dy,
+                                          float dz, float raw[3]) {
+    raw[0] = raw[1] = raw[2] = 0.5f;
+    if (stride) {
+        constexpr int EPC = STG == CS_STORE_F32 ? 4 : 8;  // elements per chunk
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(ssh) + t * stride;
+        uint4 ch = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j < nb) {
+                float gx, gy, gz;
+                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int w = 3 * j + c;
+                    if (w % EPC == 0) ch = s4[w / EPC];
+                    raw[c] += chunk_elem<STG>(ch, w % EPC) * Yj;
+                }
+            }
+        }
+    } else {
+        const int sb = t * shw;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j < nb) {
+                float gx, gy, gz;
+                const float Yj = sh_term(j, dx, dy, dz, gx, gy, gz);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) raw[c] += sm_param<STG>(ssh, sb + 3 * j + c) * Yj;
+            }
+        }
+    }
+}
+
 }  // namespace
 }  // namespace cs

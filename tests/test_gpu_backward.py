@@ -106,11 +106,12 @@ def test_gradient_raw_parameters():
     compare(got, ref, refp)
 
 
-def test_gradient_16bit_storage():
+@pytest.mark.parametrize("deg", [2, 3])  # SH staged element by element / in 16-byte chunks
+def test_gradient_16bit_storage(deg):
     """Float32 gradients of a float16-stored scene equal the oracle's on the widened values."""
     import torch
     import paper_2411_14974_gb300 as cs
-    sc = _blob(6, deg=2)
+    sc = _blob(6, deg=deg)
     wide = sc.copy()
     for name in FIELDS:
         setattr(wide, name, np.ascontiguousarray(
@@ -139,6 +140,36 @@ def test_gradient_surface_sh3():
     refp = [oracle.backward_image(sc, cam, st, G[0], perturb_seed=s) for s in (1, 2)]
     got, _ = gpu_grads(sc, [cam], G)
     compare(got, ref, refp)
+
+
+def test_unaligned_sh_array():
+    """SH coefficients at an address that is not 16-byte aligned (staged element by element instead
+    of in 16-byte chunks): the same image bit for bit, and the same gradients up to the order of
+    the blend backward's atomic additions."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = syn.surface_scene(27, n=6_000, sh_degree=3)
+    cam = syn.sphere_cameras(1, 128, 96, 4.0, seed=28)[0]
+    dev = torch.device("cuda:0")
+    G = torch.as_tensor(np.random.default_rng(29).uniform(-1, 1, (1, 3, 96, 128)).astype(np.float32), device=dev)
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    buf = torch.empty(t.sh.numel() + 1, dtype=torch.float32, device=dev)
+    shifted = buf[1:].view(t.sh.shape)
+    shifted.copy_(t.sh)
+    assert shifted.data_ptr() % 16 != 0
+    u = cs.SceneTensors(t.points, t.delta, t.sigma, t.opacity, shifted)
+    out = []
+    for scene in (t, u):
+        img, tf, state = cs.forward(scene, [cam], cs.Settings(), keep_state=True)
+        g = cs.backward(state, G)
+        torch.cuda.synchronize()
+        out.append((img.clone(), tf.clone(), {k: v.clone() for k, v in g.items()}))
+        state.release()
+    (ia, ta, ga), (ib, tb, gb) = out
+    assert torch.equal(ia, ib) and torch.equal(ta, tb)
+    for f in FIELDS:
+        scale = float(ga[f].abs().max()) + 1e-30
+        assert float((ga[f] - gb[f]).abs().max()) <= 1e-5 * scale, f
 
 
 def test_multi_view_gradient_is_sum_of_views():
