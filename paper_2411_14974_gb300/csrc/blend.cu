@@ -324,9 +324,6 @@ struct BwdPixels {
     uint32_t last[2];          // pairs at or beyond this index did not contribute
 };
 
-// Undoes record rec (pair index idx, NT lines) for both pixels of the lane: recovers T in front
-// of the pair, accumulates the per-pixel gradient terms into v32, and returns whether any of the
-// two pixels received a contribution.
 // The rest of eval_pair once the line values s[] of one pixel are known.
 template <int NT>
 __device__ __forceinline__ int eval_from_lines(const float (&s)[NT], float m, const float4 &h0, const Settings &st,
@@ -347,12 +344,34 @@ __device__ __forceinline__ int eval_from_lines(const float (&s)[NT], float m, co
     return p.alpha >= st.tau ? 2 : 1;
 }
 
+// Per-pair gradient words of a lane, packed: 3t + 0 = sum g_t x, 3t + 1 = sum g_t y, 3t + 2 = sum
+// g_t over the lane's two pixels (8x8-block coordinates), then dsigma', dopacity, dcolour (3); the
+// array is padded to the warp reduction's group size (16, 24 or 32 words).
+template <int NT>
+struct PackedWords {
+    static constexpr int SIG = 3 * NT, OPA = 3 * NT + 1, RGB = 3 * NT + 2, USED = 3 * NT + 5;
+    static constexpr int N = USED <= 16 ? 16 : USED <= 24 ? 24 : 32;
+    // gradient-record word of packed word l (l < USED)
+    __device__ static __forceinline__ int dest(int l) { return l < SIG ? l : l + (G_SIG - SIG); }
+};
+
+// Undoes record rec (pair index idx, NT lines) for both pixels of the lane: recovers T in front
+// of the pair, writes the lane's packed gradient words into v, and returns whether any of the two
+// pixels received a contribution.
 template <int NT, bool COUNT>
 __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint32_t idx, float lx, float ly,
-                                           const Settings &st, BwdPixels &q, float (&v32)[32],
+                                           const Settings &st, BwdPixels &q, float (&v)[PackedWords<NT>::N],
                                            unsigned long long (&cnt)[NCOUNT]) {
+    using PW = PackedWords<NT>;
     const float4 h0 = rec[0];
     bool any_on = false;
+    float gt[2][NT];  // dphi2 e_t of each pixel (0 where the pixel adds no line gradient)
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int t = 0; t < NT; ++t) gt[k][t] = 0.f;
+#pragma unroll
+    for (int w = PW::SIG; w < PW::N; ++w) v[w] = 0.f;
     // line values of both pixels from one read of each staged line (the lower pixel's block origin
     // is the record's second C)
     float sv[2][NT];
@@ -380,31 +399,71 @@ __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint3
         const float dalpha = q.G0[k] * (Tn * c.x - q.S0[k] * inv) + q.G1[k] * (Tn * c.y - q.S1[k] * inv) +
                              q.G2[k] * (Tn * c.z - q.S2[k] * inv);
         const float ta = Tn * p.alpha;
-        v32[G_RGB] += q.G0[k] * ta;
-        v32[G_RGB + 1] += q.G1[k] * ta;
-        v32[G_RGB + 2] += q.G2[k] * ta;
+        v[PW::RGB] += q.G0[k] * ta;
+        v[PW::RGB + 1] += q.G1[k] * ta;
+        v[PW::RGB + 2] += q.G2[k] * ta;
         q.S0[k] = fmaf(ta, c.x, q.S0[k]);
         q.S1[k] = fmaf(ta, c.y, q.S1[k]);
         q.S2[k] = fmaf(ta, c.z, q.S2[k]);
         q.Tc[k] = Tn;
         if (p.oI < st.alpha_max) {
-            v32[G_OPA] += dalpha * p.I;
+            v[PW::OPA] += dalpha * p.I;
             const float dI = dalpha * h0.z;
             // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
             const float dx = -dI * LN2 * p.z * p.I * p.I;
-            v32[G_SIG] += dx * p.phi2;
+            v[PW::SIG] += dx * p.phi2;
             const float dphi2 = dx * h0.x * rcp(p.S);
-            const float ly8 = ly + 4.0f * k;
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-                const float gt = dphi2 * p.e[t];
-                v32[3 * t] = fmaf(gt, lx, v32[3 * t]);
-                v32[3 * t + 1] = fmaf(gt, ly8, v32[3 * t + 1]);
-                v32[3 * t + 2] += gt;
-            }
+            for (int t = 0; t < NT; ++t) gt[k][t] = dphi2 * p.e[t];
         }
     }
+    // the two pixels share x; the lower one's y is 4 more
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const float gs = gt[0][t] + gt[1][t];
+        v[3 * t] = gs * lx;
+        v[3 * t + 1] = fmaf(gs, ly, 4.0f * gt[1][t]);
+        v[3 * t + 2] = gs;
+    }
     return any_on;
+}
+
+// Reduce-scatter of N = 8, 16 or 32 values over the warp: returns, in lane l, the warp sum of
+// v[l % N].  Recursive halving over lane bits log2(N) - 1 .. 0 (N - 1 shuffles), then a butterfly
+// over the remaining lane bits (5 - log2(N) shuffles).
+template <int N>
+__device__ __forceinline__ float reduce_scatter(float (&v)[N], int lane) {
+#pragma unroll
+    for (int h = N / 2; h >= 1; h >>= 1) {
+        const bool upper = (lane & h) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const float send = upper ? v[q] : v[q + h];
+            const float keep = upper ? v[q + h] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+        }
+    }
+    float x = v[0];
+#pragma unroll
+    for (int m = N; m < 32; m <<= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+    return x;
+}
+
+// lane l < USED receives the warp sum of packed word l
+template <int N>
+__device__ __forceinline__ float reduce_words(float (&v)[N], int lane) {
+    if constexpr (N == 24) {
+        float lo[16], hi[8];
+#pragma unroll
+        for (int w = 0; w < 16; ++w) lo[w] = v[w];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) hi[w] = v[16 + w];
+        const float a = reduce_scatter<16>(lo, lane);
+        const float b = reduce_scatter<8>(hi, lane);
+        return lane < 16 ? a : b;
+    } else {
+        return reduce_scatter<N>(v, lane);
+    }
 }
 
 template <bool COUNT, int K>
@@ -469,37 +528,23 @@ __global__ void __launch_bounds__(BWD_THREADS, 5) k_blend_backward(BlendArgs a, 
             bits &= bits - 1;
             const float4 *rec = wrec + j * SREC;
             const uint32_t idx = sidx[j];
-            // per-pixel terms in gradient-record word order, summed over this lane's two pixels
-            // (8x8-block coordinates): 3t+0 = g_t x, 3t+1 = g_t y, 3t+2 = g_t, 24 dsigma',
-            // 25 dopacity, 26..28 dcolour
-            float v32[32];
-#pragma unroll
-            for (int w2 = 0; w2 < 32; ++w2) v32[w2] = 0.f;
-            const bool any_on = bwd_record<K, COUNT>(rec, idx, lx, ly, st, q, v32, cnt);
+            using PW = PackedWords<K>;
+            float v[PW::N];
+            const bool any_on = bwd_record<K, COUNT>(rec, idx, lx, ly, st, q, v, cnt);
             if (!__any_sync(0xffffffffu, any_on)) continue;
-            // reduce-scatter across the warp: after five halvings lane l holds the warp sum of v32[l]
-#pragma unroll
-            for (int h = 16; h >= 1; h >>= 1) {
-                const bool upper = (lane & h) != 0;
-#pragma unroll
-                for (int q = 0; q < h; ++q) {
-                    const float send = upper ? v32[q] : v32[q + h];
-                    const float keep = upper ? v32[q + h] : v32[q];
-                    v32[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-                }
-            }
-            float word = v32[0];
+            // lane l < PW::USED: the warp sum of packed word l
+            float word = reduce_words<PW::N>(v, lane);
             // s = A (x8 + ox - ax) + B (y8 + oy - ay) + C: dA = sum(g x8) + (ox - ax) sum(g), dB likewise
             const float g2 = __shfl_down_sync(0xffffffffu, word, 2);
             const float g1 = __shfl_down_sync(0xffffffffu, word, 1);
             const uint32_t r = __float_as_uint(rec[1].w);
-            if (lane < 24) {
+            if (lane < PW::SIG) {
                 const int slot = lane % 3;
                 if (slot == 0) word = fmaf(rec[2].x, g2, word);
                 else if (slot == 1) word = fmaf(rec[2].y, g1, word);
             }
-            if (lane < 29 && word != 0.f)
-                atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + lane, word);
+            if (lane < PW::USED && word != 0.f)
+                atomicAdd(reinterpret_cast<float *>(grads + (size_t)r * (GRAD_WORDS / 4)) + PW::dest(lane), word);
         }
         __syncwarp();
     }

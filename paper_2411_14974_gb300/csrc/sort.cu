@@ -25,6 +25,7 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 constexpr int SPINE_THREADS = 1024;
+constexpr int SCAN_INLINE_BLOCKS = 1024;  // up to this many blocks, no spine kernel
 
 constexpr int RADIX_THREADS = 256;
 constexpr int RADIX_WARPS = RADIX_THREADS / 32;
@@ -100,11 +101,24 @@ __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(unsigned long long
     if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
+// INLINE: partial holds the blocks' plain sums and every block adds up those in front of it (no
+// spine kernel; used up to SCAN_INLINE_BLOCKS blocks), the last block writing the total
+template <bool INLINE>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__restrict__ in,
                                                             const uint32_t *__restrict__ gather, int64_t n,
                                                             const unsigned long long *__restrict__ partial,
-                                                            uint32_t *__restrict__ out) {
+                                                            uint32_t *__restrict__ out,
+                                                            unsigned long long *__restrict__ total_out) {
     __shared__ unsigned long long sh[32];
+    unsigned long long prefix;
+    if (INLINE) {
+        unsigned long long s = 0, tot;
+        for (int64_t b = threadIdx.x; b < (int64_t)blockIdx.x; b += SCAN_THREADS) s += partial[b];
+        (void)block_exclusive_scan(s, sh, tot);
+        prefix = tot;
+    } else {
+        prefix = partial[blockIdx.x];
+    }
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;  // blocked
     uint32_t v[SCAN_ITEMS];
     unsigned long long s = 0;
@@ -114,12 +128,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__re
         s += v[j];
     }
     unsigned long long tot;
-    unsigned long long run = block_exclusive_scan(s, sh, tot) + partial[blockIdx.x];
+    unsigned long long run = block_exclusive_scan(s, sh, tot) + prefix;
 #pragma unroll
     for (int j = 0; j < SCAN_ITEMS; ++j) {
         if (base + j < n) out[base + j] = (uint32_t)run;
         run += v[j];
     }
+    if (INLINE && total_out && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total_out = prefix + tot;
 }
 
 // ---- radix sort -----------------------------------------------------------------------------
@@ -367,9 +382,14 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather, ui
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp);
-    k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(tmp, nb, total_dev);
-    k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out);
-    count_launches(3);
+    if (nb <= SCAN_INLINE_BLOCKS) {
+        k_scan_down<true><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out, total_dev);
+        count_launches(2);
+    } else {
+        k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(tmp, nb, total_dev);
+        k_scan_down<false><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out, nullptr);
+        count_launches(3);
+    }
     return cudaGetLastError();
 }
 
