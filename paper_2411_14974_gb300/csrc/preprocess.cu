@@ -262,12 +262,22 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
         w[R_RGB + 0] = fmaxf(raw[0], 0.f);
         w[R_RGB + 1] = fmaxf(raw[1], 0.f);
         w[R_RGB + 2] = fmaxf(raw[2], 0.f);
-        float4 *dst = out.records + rec * (REC_WORDS / 4);
+    }
+    // The SH buffer, read by now, takes the block's records (8 chunks each at an odd stride of 9);
+    // they are written out with coalesced stores below.
+    constexpr int RC = REC_WORDS / 4, RS = RC + 1;
+    static_assert(PRE_THREADS * RS * 4 <= PRE_THREADS * SH_STAGE_WORDS, "records fit the SH buffer");
+    float4 *srec = reinterpret_cast<float4 *>(ssh);
+    __shared__ uint8_t sdrawn[PRE_THREADS];
+    __syncthreads();
+    if (drawn) {
 #pragma unroll
-        for (int q = 0; q < REC_WORDS / 4; ++q) dst[q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        for (int q = 0; q < RC; ++q)
+            srec[threadIdx.x * RS + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         out.bboxes[rec] = bbox;
         out.radii[rec] = radius;
     }
+    sdrawn[threadIdx.x] = drawn ? 1 : 0;
     if (i < n) {
         out.depth_keys[rec] = drawn ? depth_key : 0xffffffffu;
         out.counts[rec] = drawn ? count : 0u;
@@ -284,6 +294,11 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
         bmin_inv[threadIdx.x >> 5] = wmin_inv;
     }
     __syncthreads();
+    {
+        float4 *dst = out.records + (vd.rec_base + i0) * RC;
+        for (int q = threadIdx.x; q < cnt * RC; q += PRE_THREADS)
+            if (sdrawn[q / RC]) dst[q] = srec[(q / RC) * RS + q % RC];
+    }
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
         uint32_t mx = 0, mi = 0;
