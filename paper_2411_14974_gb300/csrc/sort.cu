@@ -146,15 +146,39 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t 
     const uint32_t nbins = 1u << nbits, mask = nbins - 1;
     for (int i = threadIdx.x; i < RADIX_WARPS * (1 << RADIX_MAX_BITS); i += RADIX_THREADS) (&cnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t seg = (int64_t)blockIdx.x * RADIX_TILE + (int64_t)w * (RADIX_ITEMS * 32);
-#pragma unroll 4
-    for (int j = 0; j < RADIX_ITEMS; ++j) {
-        const int64_t idx = seg + j * 32 + lane;
-        const uint32_t d = idx < n ? (keys[idx] >> shift) & mask : 0xffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d != 0xffffu && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
-        __syncwarp();
+    // counts only (no ranks): each thread takes RADIX_ITEMS consecutive keys (16-byte loads) and
+    // adds every run of equal digits with one shared atomic into its warp's histogram
+    (void)lane;
+    const int64_t base = (int64_t)blockIdx.x * RADIX_TILE + (int64_t)threadIdx.x * RADIX_ITEMS;
+    uint32_t k[RADIX_ITEMS];
+    int nk = 0;
+    if (base + RADIX_ITEMS <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+        for (int q = 0; q < RADIX_ITEMS / 4; ++q) {
+            const uint4 v = src[q];
+            k[4 * q] = v.x; k[4 * q + 1] = v.y; k[4 * q + 2] = v.z; k[4 * q + 3] = v.w;
+        }
+        nk = RADIX_ITEMS;
+    } else {
+#pragma unroll
+        for (int q = 0; q < RADIX_ITEMS; ++q) k[q] = base + q < n ? keys[base + q] : 0u;
+        nk = base < n ? (int)(n - base) : 0;
     }
+    uint32_t cur = 0xffffffffu, run = 0;
+#pragma unroll
+    for (int q = 0; q < RADIX_ITEMS; ++q) {
+        if (q < nk) {
+            const uint32_t d = (k[q] >> shift) & mask;
+            if (d != cur) {
+                if (run) atomicAdd(&cnt[w][cur], run);
+                cur = d;
+                run = 0;
+            }
+            ++run;
+        }
+    }
+    if (run) atomicAdd(&cnt[w][cur], run);
     __syncthreads();
     for (uint32_t d = threadIdx.x; d < nbins; d += RADIX_THREADS) {
         uint32_t s = 0;
@@ -284,30 +308,49 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
                        uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t r = 0, cnt = 0, area = 0, o = 0, hi = 0, tiles_x = 0;
+    uint32_t r = 0, cnt = 0, area = 0, o = 0xffffffffu, hi = 0, tiles_x = 0;
     uint2 rc = make_uint2(0, 0);
     if (j < n_records) {
         r = sorted[j];
         cnt = counts[r];
+        o = offsets[j];
         if (cnt != 0) {
             rc = rects[r];
             area = ((rc.x >> 16) - (rc.x & 0xffffu) + 1) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1);
             const int v = view_of_record(views, n_views, r);
             hi = (uint32_t)v << local_bits;
             tiles_x = (uint32_t)views[v].tiles_x;
-            o = offsets[j];
         }
     }
     const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
+    const bool full = cnt != 0 && cnt == area;  // every tile of the rectangle
     const bool coop = cnt != 0 && cnt != area && area > (uint32_t)SAT_SERIAL_TILES;
-    if (cnt != 0 && cnt == area) {  // every tile of the rectangle
-        for (uint32_t ty = ty0; ty <= ty1; ++ty)
-            for (uint32_t tx = tx0; tx <= tx1; ++tx) {
-                keys[o] = hi | (ty * tiles_x + tx);
-                vals[o] = r;
-                ++o;
+    if (__any_sync(0xffffffffu, full)) {
+        // The warp's records, consecutive in depth order, own the contiguous output range from
+        // lane 0's offset to the end of its last record; the full rectangles' pairs are written
+        // with consecutive addresses, output p belonging to the last lane whose offset is <= p
+        // (offsets do not decrease with the lane; lanes past the end hold 0xffffffff).
+        const uint32_t wb = __shfl_sync(0xffffffffu, o, 0);
+        const uint32_t we = __reduce_max_sync(0xffffffffu, j < n_records ? o + cnt : 0u);
+        for (uint32_t p0 = wb; p0 < we; p0 += 32) {
+            const uint32_t p = p0 + (uint32_t)lane;
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (__shfl_sync(0xffffffffu, o, s + step) <= p) s += step;
+            const bool fs = __shfl_sync(0xffffffffu, full, s);
+            const uint32_t os = __shfl_sync(0xffffffffu, o, s), rs = __shfl_sync(0xffffffffu, r, s);
+            const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, s), ry = __shfl_sync(0xffffffffu, rc.y, s);
+            const uint32_t hs = __shfl_sync(0xffffffffu, hi, s), txs = __shfl_sync(0xffffffffu, tiles_x, s);
+            if (p < we && fs) {
+                const uint32_t k = p - os, wd = (rx >> 16) - (rx & 0xffffu) + 1;
+                const uint32_t ty = (ry & 0xffffu) + k / wd, tx = (rx & 0xffffu) + k % wd;
+                keys[p] = hs | (ty * txs + tx);
+                vals[p] = rs;
             }
-    } else if (cnt != 0 && !coop) {  // small rectangle: the same exact test on the same record values
+        }
+    }
+    if (cnt != 0 && !full && !coop) {  // small rectangle: the same exact test on the same record values
         float w[REC_WORDS];
         const float4 *rec = records + (size_t)r * (REC_WORDS / 4);
 #pragma unroll
