@@ -333,6 +333,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     const int view_bits = bits_for((uint64_t)V);
     if (local_bits + view_bits > 32) return fail(CS_ERR_ARG, "too many views and tiles for a 32-bit pair key");
     s->local_bits = local_bits;
+    // block masks ride in the pair keys' free high bits when there are enough of them
+    s->mask_shift = local_bits + view_bits + BLOCK_MASK_BITS <= 32 ? local_bits + view_bits : 0;
 
     CS_TRY(pool_alloc(ctx, (void **)&s->views_dev, sizeof(ViewDesc) * V, stream), "alloc views");
     CS_TRY(pool_alloc(ctx, (void **)&s->records, (size_t)R * REC_WORDS * 4, stream), "alloc records");
@@ -418,8 +420,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
-        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii, R,
-                                 local_bits, s->pair_keys, s->pair_vals, stream),
+        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii, s->bboxes,
+                                 R, local_bits, s->mask_shift, s->pair_keys, s->pair_vals, stream),
                "emit pairs");
         pool_free(radii, stream);
         radii = nullptr;
@@ -441,12 +443,14 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             uint32_t *t = s->pair_keys; s->pair_keys = pk_b; pk_b = t;
             t = s->pair_vals; s->pair_vals = pv_b; pv_b = t;
         }
-        CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->views_dev, local_bits, s->ranges, tiles, stream),
+        CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->views_dev, local_bits, s->mask_shift, s->ranges, tiles,
+                                  stream),
                "tile ranges");
     }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);
-        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles, s->k};
+        BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles, s->k,
+                    s->pair_keys, s->mask_shift};
         CS_TRY(launch_blend_forward(a, stream), "blend");
     }
     for (int v = 0; v < V; ++v) {
@@ -535,7 +539,8 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
-            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k};
+            BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k,
+                        s->pair_keys, s->mask_shift};
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }
@@ -603,6 +608,11 @@ extern "C" cs_status cs_state_copy(const cs_fwd_state *s, int32_t which, void *h
         e = cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail_cuda(e, "copy");
     }
+    if (which == CS_ARR_PAIR_KEYS && s->mask_shift) {  // the documented layout: block masks removed
+        uint32_t *d = (uint32_t *)host_dst;
+        const uint32_t keep = (1u << s->mask_shift) - 1u;
+        for (int64_t q = 0; q < s->n_pairs; ++q) d[q] &= keep;
+    }
     return CS_OK;
 }
 
@@ -668,7 +678,8 @@ extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, cons
     cudaError_t e = pool_alloc(ctx, (void **)&dc, 12 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, 12 * sizeof(unsigned long long), stream);
     const int V = (int)s->views.size();
-    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k};
+    BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k,
+                        s->pair_keys, s->mask_shift};
     if (e == cudaSuccess) e = launch_blend_forward(a, stream, dc);
     if (e == cudaSuccess && dL_dimage && s->n_records) {
         e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);

@@ -188,7 +188,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // decreasing order), and advances pos past what it consumed.  Warp-uniform except the loads.
 template <bool BACK>
 __device__ __forceinline__ int gather_candidates(const BlendArgs &a, float x0, float x1, float y0, float y1,
-                                                 uint32_t lo, uint32_t hi, uint32_t &pos, uint32_t *sidx, int lane) {
+                                                 uint32_t block_bits, uint32_t lo, uint32_t hi, uint32_t &pos,
+                                                 uint32_t *sidx, int lane) {
     const uint32_t lt = lanemask_lt();
     int nh = 0;
     while (nh < 32 && (BACK ? pos > lo : pos < hi)) {
@@ -196,8 +197,12 @@ __device__ __forceinline__ int gather_candidates(const BlendArgs &a, float x0, f
         const uint32_t i = BACK ? pos - 1 - (uint32_t)lane : pos + (uint32_t)lane;
         bool hit = false;
         if ((uint32_t)lane < avail) {
-            const float4 bb = __ldg(a.bboxes + a.pair_vals[i]);
-            hit = !(bb.z < x0 || bb.x > x1 || bb.w < y0 || bb.y > y1);
+            if (a.mask_shift) {  // the pair key carries the box test of every 8x4 block of the tile
+                hit = ((__ldg(a.pair_keys + i) >> a.mask_shift) & block_bits) != 0u;
+            } else {
+                const float4 bb = __ldg(a.bboxes + a.pair_vals[i]);
+                hit = !(bb.z < x0 || bb.x > x1 || bb.w < y0 || bb.y > y1);
+            }
         }
         const uint32_t hits = __ballot_sync(0xffffffffu, hit);
         const int room = 32 - nh;
@@ -252,8 +257,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
     uint32_t pos = range.x;
     while (pos < range.y) {
         if (__all_sync(0xffffffffu, done)) break;
-        const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, range.x, range.y, pos,
-                                                sidx, lane);
+        // this warp's 8x4 block is column w & 1, row w >> 1 of the tile: mask bit w
+        const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, 1u << w, range.x, range.y,
+                                                pos, sidx, lane);
         bool pass = false;
         if (lane < nh) pass = stage_record<4, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();
@@ -517,8 +523,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 5) k_blend_backward(BlendArgs a, 
     const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
     uint32_t pos = max(wend, range.x);
     while (pos > range.x) {
-        const int nh = gather_candidates<true>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 7.5f, range.x, range.y, pos,
-                                               sidx, lane);
+        // this warp's 8x8 block is the 8x4 blocks of column w & 1, rows 2 (w >> 1) and 2 (w >> 1) + 1
+        const uint32_t bbits = 5u << (4 * (w >> 1) + (w & 1));
+        const int nh = gather_candidates<true>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 7.5f, bbits, range.x, range.y,
+                                               pos, sidx, lane);
         bool pass = false;
         if (lane < nh) pass = stage_record<8, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
         __syncwarp();

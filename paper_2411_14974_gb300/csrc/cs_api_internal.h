@@ -36,6 +36,7 @@ struct cs_fwd_state {
     int64_t n_records = 0, n_pairs = 0;
     uint32_t n_tiles = 0;
     int local_bits = 0;  // pair key = view << local_bits | tile index within the view
+    int mask_shift = 0;  // block masks above the view bits (0: none)
     float4 *records = nullptr;
     uint32_t *depth_keys = nullptr;
     uint2 *rects = nullptr;

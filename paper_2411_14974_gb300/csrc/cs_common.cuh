@@ -110,13 +110,18 @@ cudaError_t launch_depth_sort_input(const uint32_t *depth_keys, int64_t n, uint3
 // keys[j] = view index of record sorted_records[j]
 cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
                              uint32_t *keys, cudaStream_t s);
-// pair key = view << local_bits | tile index within the view
+// pair key = view << local_bits | tile index within the view, and, when mask_shift > 0, the pair's
+// block mask << mask_shift: bit 2 q + c set when the record's pixel box holds a pixel centre of the
+// tile's 8x4 block in column c, row q (the blocks of the forward blend's warps).  The tile sort
+// orders local_bits only, so the mask bits travel with their pair.
+constexpr int BLOCK_MASK_BITS = 8;
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
-                              const float4 *records, const float *radii, int64_t n_records, int local_bits,
-                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s);
+                              const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
+                              int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
+                              cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
-                               uint2 *ranges, int64_t n_tiles, cudaStream_t s);
+                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s);
 
 struct BlendArgs {
     const ViewDesc *views;
@@ -128,6 +133,8 @@ struct BlendArgs {
     Settings st;
     uint32_t n_tiles;
     int k;  // points per convex: at most k hull lines per record
+    const uint32_t *pair_keys;  // with block masks when mask_shift > 0
+    int mask_shift;             // 0: no masks, the gather tests the records' pixel boxes
 };
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);

@@ -301,21 +301,44 @@ __global__ void k_view_keys(const ViewDesc *__restrict__ views, int n_views, con
 // Emits the pairs of record sorted[j] at offsets[j]: every tile of its rectangle when all are kept
 // (count == area), else the tiles the exact test keeps, tested by the thread itself for small
 // rectangles and by the whole warp, 32 tiles at a time, for large ones.
+// bit 2 q + c: the pixel box bb holds a pixel centre of the 8x4 block in column c, row q of tile
+// (tx, ty), with the blend gather's test and values
+__device__ __forceinline__ uint32_t block_mask(const float4 &bb, uint32_t tx, uint32_t ty) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float x0 = (float)(tx * TILE + 8 * c) + 0.5f, x1 = x0 + 7.0f;
+        if (bb.z < x0 || bb.x > x1) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float y0 = (float)(ty * TILE + 4 * q) + 0.5f, y1 = y0 + 3.0f;
+            if (!(bb.w < y0 || bb.y > y1)) m |= 1u << (2 * q + c);
+        }
+    }
+    return m;
+}
+
 __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
                        const uint2 *__restrict__ rects, const float4 *__restrict__ records,
-                       const float *__restrict__ radii, int64_t n_records, int local_bits,
-                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                       const float *__restrict__ radii, const float4 *__restrict__ bboxes, int64_t n_records,
+                       int local_bits, int mask_shift, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    // the block mask of tile (tx, ty) for box bb, at its place in the key (0 without masks)
+    auto mask_bits = [&](const float4 &bb, uint32_t tx, uint32_t ty) -> uint32_t {
+        return mask_shift ? block_mask(bb, tx, ty) << mask_shift : 0u;
+    };
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     uint32_t r = 0, cnt = 0, area = 0, o = 0xffffffffu, hi = 0, tiles_x = 0;
     uint2 rc = make_uint2(0, 0);
+    float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j < n_records) {
         r = sorted[j];
         cnt = counts[r];
         o = offsets[j];
         if (cnt != 0) {
             rc = rects[r];
+            if (mask_shift) bb = bboxes[r];
             area = ((rc.x >> 16) - (rc.x & 0xffffu) + 1) * ((rc.y >> 16) - (rc.y & 0xffffu) + 1);
             const int v = view_of_record(views, n_views, r);
             hi = (uint32_t)v << local_bits;
@@ -342,10 +365,15 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
             const uint32_t os = __shfl_sync(0xffffffffu, o, s), rs = __shfl_sync(0xffffffffu, r, s);
             const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, s), ry = __shfl_sync(0xffffffffu, rc.y, s);
             const uint32_t hs = __shfl_sync(0xffffffffu, hi, s), txs = __shfl_sync(0xffffffffu, tiles_x, s);
+            float4 bs;
+            bs.x = __shfl_sync(0xffffffffu, bb.x, s);
+            bs.y = __shfl_sync(0xffffffffu, bb.y, s);
+            bs.z = __shfl_sync(0xffffffffu, bb.z, s);
+            bs.w = __shfl_sync(0xffffffffu, bb.w, s);
             if (p < we && fs) {
                 const uint32_t k = p - os, wd = (rx >> 16) - (rx & 0xffffu) + 1;
                 const uint32_t ty = (ry & 0xffffu) + k / wd, tx = (rx & 0xffffu) + k % wd;
-                keys[p] = hs | (ty * txs + tx);
+                keys[p] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
                 vals[p] = rs;
             }
         }
@@ -363,7 +391,7 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
         for (uint32_t ty = ty0; ty <= ty1; ++ty)
             for (uint32_t tx = tx0; tx <= tx1; ++tx)
                 if (tile_kept(w + R_LINES, T, w[R_AX], w[R_AY], rk, (int)tx, (int)ty)) {
-                    keys[o] = hi | (ty * tiles_x + tx);
+                    keys[o] = mask_bits(bb, tx, ty) | hi | (ty * tiles_x + tx);
                     vals[o] = r;
                     ++o;
                 }
@@ -376,6 +404,11 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
         const uint32_t txs = __shfl_sync(0xffffffffu, tiles_x, src);
         const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, src), ry = __shfl_sync(0xffffffffu, rc.y, src);
         uint32_t os = __shfl_sync(0xffffffffu, o, src);
+        float4 bs;
+        bs.x = __shfl_sync(0xffffffffu, bb.x, src);
+        bs.y = __shfl_sync(0xffffffffu, bb.y, src);
+        bs.z = __shfl_sync(0xffffffffu, bb.z, src);
+        bs.w = __shfl_sync(0xffffffffu, bb.w, src);
         float w[REC_WORDS];
         const float4 *rec = records + (size_t)rs * (REC_WORDS / 4);
 #pragma unroll
@@ -394,7 +427,7 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
             const uint32_t ball = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const uint32_t at = os + (uint32_t)__popc(ball & ((1u << lane) - 1u));
-                keys[at] = hs | (ty * txs + tx);
+                keys[at] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
                 vals[at] = rs;
             }
             os += (uint32_t)__popc(ball);
@@ -404,13 +437,13 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
 
 // [start, end) of every (view, tile) group of the sorted pairs, stored at the global tile index
 __global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, const ViewDesc *__restrict__ views,
-                         int local_bits, uint2 *__restrict__ ranges) {
+                         int local_bits, uint32_t key_mask, uint2 *__restrict__ ranges) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t k = keys[i];
+    const uint32_t k = keys[i] & key_mask;
     const uint32_t g = views[k >> local_bits].tile_base + (k & ((1u << local_bits) - 1u));
-    if (i == 0 || keys[i - 1] != k) ranges[g].x = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[g].y = (uint32_t)(i + 1);
+    if (i == 0 || (keys[i - 1] & key_mask) != k) ranges[g].x = (uint32_t)i;
+    if (i == n - 1 || (keys[i + 1] & key_mask) != k) ranges[g].y = (uint32_t)(i + 1);
 }
 
 }  // namespace
@@ -487,21 +520,25 @@ cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint3
 
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
-                              const float4 *records, const float *radii, int64_t n_records, int local_bits,
-                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s) {
+                              const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
+                              int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
+                              cudaStream_t s) {
     if (n_records <= 0) return cudaSuccess;
+    if (mask_shift < 0 || (mask_shift > 0 && mask_shift + BLOCK_MASK_BITS > 32)) return cudaErrorInvalidValue;
     k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
-                                                               rects, records, radii, n_records, local_bits,
-                                                               pair_keys, pair_vals);
+                                                               rects, records, radii, bboxes, n_records, local_bits,
+                                                               mask_shift, pair_keys, pair_vals);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
-                               uint2 *ranges, int64_t n_tiles, cudaStream_t s) {
+                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
-    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, ranges);
+    const uint32_t key_mask = mask_shift ? (1u << mask_shift) - 1u : 0xffffffffu;
+    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, key_mask,
+                                                              ranges);
     count_launches(1);
     return cudaGetLastError();
 }

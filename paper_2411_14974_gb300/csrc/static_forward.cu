@@ -147,14 +147,17 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const uint32_t *sorted = in_b ? vb : va;
     if (e == cudaSuccess) e = launch_exclusive_scan(counts, sorted, offsets, R, nullptr, scan_tmp, stream);
     const int local_bits = bits_for(tiles);
-    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, R, local_bits, pk, pv, stream);
+    const int mask_shift = local_bits + BLOCK_MASK_BITS <= 32 ? local_bits : 0;
+    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, bboxes, R, local_bits,
+                          mask_shift, pk, pv, stream);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);
     const uint32_t *keys = in_b ? pk2 : pk;
     const uint32_t *vals = in_b ? pv2 : pv;
-    if (e == cudaSuccess) e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, ranges, tiles, stream);
+    if (e == cudaSuccess)
+        e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, mask_shift, ranges, tiles, stream);
     if (e == cudaSuccess) {
-        BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles, scene->k};
+        BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles, scene->k, keys, mask_shift};
         e = launch_blend_forward(a, stream);
     }
     if (e != cudaSuccess) return fail_cuda(e, "cs_forward_static");
