@@ -473,7 +473,7 @@ __device__ __forceinline__ float reduce_words(float (&v)[N], int lane) {
 }
 
 template <bool COUNT, int K>
-__global__ void __launch_bounds__(BWD_THREADS, 5) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
+__global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
     __shared__ float4 srec[BWD_THREADS / 32][32 * SREC];
