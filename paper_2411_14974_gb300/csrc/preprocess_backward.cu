@@ -15,7 +15,7 @@ namespace {
 // once it has read them); with several views, convexes are shared between views and use global
 // atomics.
 template <int K, int DEG, bool ATOMIC, int STG>
-__global__ void __launch_bounds__(PRE_THREADS, 4) k_preprocess_backward(const ViewDesc *__restrict__ views, Settings st,
+__global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const ViewDesc *__restrict__ views, Settings st,
                                                                      const float4 *__restrict__ records,
                                                                      const uint32_t *__restrict__ counts,
                                                                      const float4 *__restrict__ grads,
