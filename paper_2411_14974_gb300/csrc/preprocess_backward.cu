@@ -54,6 +54,18 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
     };
     const int64_t i = i0 + threadIdx.x;
     const int64_t rec = vd.rec_base + i;
+    // the lines this thread reads after the barrier (its gradient record, the record's colour and
+    // hull, its points) and the block's SH gradients updated at the end are requested into L2 while
+    // the block waits for its staged SH
+    if (i < vd.n) {
+        prefetch_l2(grads + rec * (GRAD_WORDS / 4));
+        prefetch_l2(records + rec * (REC_WORDS / 4));
+        const char *pp = reinterpret_cast<const char *>(vd.points) + (size_t)i * PW * esz;
+        prefetch_l2(pp);
+        prefetch_l2(pp + PW * esz - 1);
+    }
+    if (IN_PLACE && out.dsh)
+        for (int q = threadIdx.x * 32; q < cnt * SW; q += PRE_THREADS * 32) prefetch_l2(out.dsh + i0 * SW + q);
     const bool live = i < vd.n && counts[rec] != 0;
     cp_async_wait_all();
     __syncthreads();  // staged SH (and, with one view, the gathered gradients) visible to the block
