@@ -397,10 +397,14 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_words * 8, stream), "alloc");
         {
             StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
-            CS_TRY(launch_depth_sort_input(s->depth_keys, R, key_min, sort_keys_a, sort_vals_a, stream), "sort input");
-            CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
-                                    scan_tmp, &in_b, stream),
-                   "depth sort");
+            if (depth_bits > 0 && R > 1) {  // the first pass reads the keys rebased, values = indices
+                CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
+                                        scan_tmp, &in_b, stream, s->depth_keys, key_min),
+                       "depth sort");
+            } else {
+                CS_TRY(launch_depth_sort_input(s->depth_keys, R, key_min, sort_keys_a, sort_vals_a, stream),
+                       "sort input");
+            }
         }
         uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;
         if (V > 1) {

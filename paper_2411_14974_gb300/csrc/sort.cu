@@ -138,9 +138,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__re
 }
 
 // ---- radix sort -----------------------------------------------------------------------------
+// key_sub is subtracted from every key read (the first pass of a rebased sort; 0 otherwise)
 __global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t *__restrict__ keys, int64_t n,
-                                                                 int shift, int nbits, uint32_t *__restrict__ hist,
-                                                                 int64_t nblocks) {
+                                                                 int shift, int nbits, uint32_t key_sub,
+                                                                 uint32_t *__restrict__ hist, int64_t nblocks) {
     __shared__ uint32_t cnt[RADIX_WARPS][1 << RADIX_MAX_BITS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t nbins = 1u << nbits, mask = nbins - 1;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t 
 #pragma unroll
     for (int q = 0; q < RADIX_ITEMS; ++q) {
         if (q < nk) {
-            const uint32_t d = (k[q] >> shift) & mask;
+            const uint32_t d = ((k[q] - key_sub) >> shift) & mask;
             if (d != cur) {
                 if (run) atomicAdd(&cnt[w][cur], run);
                 cur = d;
@@ -188,9 +189,11 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t 
     }
 }
 
+// key_sub: subtracted from every key read, and the rebased key written (first pass of a rebased
+// sort); vals_in NULL: the values are the keys' indices
 __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t *__restrict__ keys_in,
                                                                  const uint32_t *__restrict__ vals_in, int64_t n,
-                                                                 int shift, int nbits,
+                                                                 int shift, int nbits, uint32_t key_sub,
                                                                  const uint32_t *__restrict__ offsets,
                                                                  int64_t nblocks, uint32_t *__restrict__ keys_out,
                                                                  uint32_t *__restrict__ vals_out) {
@@ -214,8 +217,8 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
     for (int j = 0; j < RADIX_ITEMS; ++j) {
         const int64_t idx = seg + j * 32 + lane;
         const bool valid = idx < n;
-        key[j] = valid ? keys_in[idx] : 0u;
-        val[j] = valid ? vals_in[idx] : 0u;
+        key[j] = valid ? keys_in[idx] - key_sub : 0u;
+        val[j] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
         const uint32_t d = valid ? (key[j] >> shift) & mask : 0xffffu;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t base = 0;
@@ -476,27 +479,33 @@ size_t radix_tmp_words(int64_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
-                             cudaStream_t s) {
+                             cudaStream_t s, const uint32_t *first_keys, uint32_t first_key_sub) {
     *result_in_b = false;
     if (n <= 1 || bits <= 0) return cudaSuccess;
     const int64_t nb = (n + RADIX_TILE - 1) / RADIX_TILE;
     const int passes = (bits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
     uint32_t *hist = tmp;
     uint32_t *offs = tmp + nb * (1 << RADIX_MAX_BITS);
-    uint32_t *kin = keys_a, *vin = vals_a, *kout = keys_b, *vout = vals_b;
+    const uint32_t *kin = first_keys ? first_keys : keys_a;
+    const uint32_t *vin = first_keys ? nullptr : vals_a;
+    uint32_t *kout = keys_b, *vout = vals_b;
     int shift = 0;
     for (int p = 0; p < passes; ++p) {
         const int w = (bits - shift + (passes - p) - 1) / (passes - p);  // spread the bits evenly
         const int64_t nh = (int64_t)(1 << w) * nb;
-        k_radix_upsweep<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, n, shift, w, hist, nb);
+        const uint32_t sub = (p == 0 && first_keys) ? first_key_sub : 0u;
+        k_radix_upsweep<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, n, shift, w, sub, hist, nb);
         cudaError_t e = launch_exclusive_scan(hist, nullptr, offs, nh, nullptr, scan_tmp, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, vin, n, shift, w, offs, nb, kout, vout);
+        k_radix_scatter<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, vin, n, shift, w, sub, offs, nb, kout, vout);
         count_launches(2);
         shift += w;
-        uint32_t *t;
-        t = kin; kin = kout; kout = t;
-        t = vin; vin = vout; vout = t;
+        // the next pass reads what this one wrote and writes the other buffer (never first_keys)
+        uint32_t *next_k = kout == keys_b ? keys_a : keys_b, *next_v = vout == vals_b ? vals_a : vals_b;
+        kin = kout;
+        vin = vout;
+        kout = next_k;
+        vout = next_v;
         *result_in_b = !*result_in_b;
     }
     return cudaGetLastError();

@@ -142,8 +142,10 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const uint32_t key_min = ~tot.key_min_inv;
     const int depth_bits = P ? bits_for((uint64_t)(tot.key_max - key_min) + 1) : 0;
     bool in_b = false;
-    e = launch_depth_sort_input(depth_keys, R, key_min, ka, va, stream);
-    if (e == cudaSuccess) e = radix_sort_pairs(ka, va, kb, vb, R, depth_bits, radix_tmp, scan_tmp, &in_b, stream);
+    if (depth_bits > 0 && R > 1)  // the first pass reads the keys rebased, values = indices
+        e = radix_sort_pairs(ka, va, kb, vb, R, depth_bits, radix_tmp, scan_tmp, &in_b, stream, depth_keys, key_min);
+    else
+        e = launch_depth_sort_input(depth_keys, R, key_min, ka, va, stream);
     const uint32_t *sorted = in_b ? vb : va;
     if (e == cudaSuccess) e = launch_exclusive_scan(counts, sorted, offsets, R, nullptr, scan_tmp, stream);
     const int local_bits = bits_for(tiles);
