@@ -293,3 +293,44 @@ def test_square_worked_example_on_gpu():
     img, _, _, _ = P.gpu_render(sc, [cam], tau=0.0, alpha_max=1.0, t_min=0.0)
     I, _ = C.square_indicator_closed_form(128, 128, 63.5, 8.0, 2.0, 0.5)
     assert np.abs(img[0, 0] - 0.5 * I).max() < 1e-5
+
+
+def _unit(rng, shape):
+    u = rng.normal(size=shape + (3,))
+    return u / np.linalg.norm(u, axis=-1, keepdims=True)
+
+
+def test_equal_depth_keys_keep_convex_order():
+    """Every convex a copy of the same points (one depth key for all; the depth sort then runs no
+    pass) with its own smoothness, sharpness, opacity and colour: ties keep convex-index order in
+    every tile, as in the oracle, and the image matches."""
+    sc = syn.blob_scene(71, n=300, radius=0.3)
+    sc.points = np.repeat(sc.points[:1], sc.n, axis=0)
+    cam = syn.blob_camera(96, 80)
+    img, tf, state, _ = P.gpu_render(sc, [cam])
+    disc = check_discrete(state, sc, cam)
+    keys = disc["depth_bits"][disc["visible"] == 1]
+    assert len(keys) == sc.n and (keys == keys[0]).all()
+    check_pairs(state, [disc], [cam])
+    ref, ill = P.oracle_reference(sc, cam)
+    check_image(img[0], ref, ill)
+
+
+def test_depth_keys_over_a_wide_range():
+    """Camera distances from 0.06 to 90 (binary32 keys that differ in their exponent bits, so the
+    depth sort orders more than 24 key bits in four passes): the pair list equals the oracle's bit
+    for bit."""
+    rng = np.random.default_rng(70)
+    n = 2000
+    depth = np.exp(rng.uniform(np.log(0.06), np.log(90.0), n))
+    ang = rng.uniform(-0.35, 0.35, (n, 2))
+    centres = np.stack([depth * np.tan(ang[:, 0]), depth * np.tan(ang[:, 1]), depth - 4.0], 1)
+    sc = syn.blob_scene(70, n=n)
+    sc.points = (centres[:, None, :] + 0.02 * depth[:, None, None] * _unit(rng, (n, sc.points.shape[1]))).astype(
+        np.float32)
+    cam = syn.blob_camera(256, 192)
+    img, tf, state, _ = P.gpu_render(sc, [cam])
+    disc = check_discrete(state, sc, cam)
+    keys = disc["depth_bits"][disc["visible"] == 1].astype(np.int64)
+    assert len(keys) > n // 2 and (int(keys.max()) ^ int(keys.min())) >> 24
+    check_pairs(state, [disc], [cam])

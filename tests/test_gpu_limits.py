@@ -80,3 +80,26 @@ def test_requests_past_the_limits_are_rejected():
         cs.forward(t, [syn.blob_camera(8, 8)] * 1025, cs.Settings())
     with pytest.raises(B.CsError):
         cs.forward(t, [syn.blob_camera(8, 8)], cs.Settings(tile_test=2))
+
+
+def test_pair_keys_without_room_for_block_masks():
+    """129 views of 4096 x 4112 (65,792 tiles each: 17 tile bits, 8 view bits) leave a pair key no
+    room for the 8-bit block mask, so the blend gathers test the records' pixel boxes instead; each
+    view of that batch renders bit for bit as it does alone (with masks).  About 52 GB of views."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = syn.blob_scene(72, n=2000, radius=0.08)
+    cams = syn.sphere_cameras(129, 4096, 4112, 4.0, seed=73)
+    tiles = (4096 // 16) * ((4112 + 15) // 16)
+    assert (len(cams) - 1).bit_length() + (tiles - 1).bit_length() + 8 > 32  # view + tile + mask bits
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    img, tf, _ = cs.forward(t, cams, cs.Settings())
+    torch.cuda.synchronize()
+    for v in (0, 64, 128):
+        one, tf1, _ = cs.forward(t, [cams[v]], cs.Settings())
+        torch.cuda.synchronize()
+        assert torch.equal(one[0], img[v]) and torch.equal(tf1[0], tf[v]), v
+        del one, tf1
+    del img, tf
+    torch.cuda.empty_cache()
