@@ -152,11 +152,13 @@ extern "C" cs_status cs_context_create(int32_t device, cs_context **out) {
     uint64_t keep = UINT64_MAX;  // keep freed memory in the pool: later calls reuse it without the driver
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     e = cudaMallocHost(&c->host_total, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->totals_ready, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (c->host_total) cudaFreeHost(c->host_total);
         cudaMemPoolDestroy(c->pool);
         delete c;
         cudaSetDevice(prev);
-        return fail_cuda(e, "cudaMallocHost");
+        return fail_cuda(e, "context set-up");
     }
     cudaSetDevice(prev);
     *out = c;
@@ -175,6 +177,7 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
     }
     for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
     if (ctx->host_total) cudaFreeHost(ctx->host_total);
+    if (ctx->totals_ready) cudaEventDestroy(ctx->totals_ready);
     cudaMemPoolTrimTo(ctx->pool, 0);
     cudaMemPoolDestroy(ctx->pool);
     cudaSetDevice(prev);
@@ -321,7 +324,6 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     unsigned long long *scan_tmp = nullptr, *total = nullptr;
     float *radii = nullptr;
     uint64_t P = 0;
-    uint32_t key_min = 0;
     int depth_bits = 0;
     bool in_b = false;
     uint32_t max_view_tiles = 1;
@@ -370,23 +372,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
                          reinterpret_cast<PreprocessStats *>(total)};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
     }
-    // the forward's one host synchronisation: the pair count (to size the pair lists) and the range
-    // of the drawn records' depth keys (the depth sort orders only the bits in which they differ)
-    CS_TRY(cudaMemcpyAsync(ctx->host_total, total, sizeof(PreprocessStats), cudaMemcpyDeviceToHost, stream),
-           "read totals");
-    CS_TRY(cudaStreamSynchronize(stream), "synchronize");
     {
-        const PreprocessStats tot = *reinterpret_cast<const PreprocessStats *>(ctx->host_total);
-        P = tot.pairs;
-        if (P >= 0xffffffffull) {
-            st_code = fail(CS_ERR_ARG, "%llu tile pairs exceed the 32-bit pair index", (unsigned long long)P);
-            goto cleanup;
-        }
-        key_min = ~tot.key_min_inv;
-        depth_bits = P ? bits_for((uint64_t)(tot.key_max - key_min) + 1) : 0;
-    }
-    // depth order of the records
-    {
+        // the depth sort's buffers (sized by the records alone) are taken while the preprocess runs
         const size_t scan_words = scan_tmp_words(R > 256 * 8 ? R : 256 * 8) + scan_tmp_words(256 * ((R + 4095) / 4096 + 1));
         CS_TRY(pool_alloc(ctx, (void **)&sort_keys_a, (size_t)R * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&sort_keys_b, (size_t)R * 4, stream), "alloc");
@@ -395,15 +382,50 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&offsets, (size_t)R * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&radix_tmp, radix_tmp_words(R) * 4, stream), "alloc");
         CS_TRY(pool_alloc(ctx, (void **)&scan_tmp, scan_words * 8, stream), "alloc");
+    }
+    // The forward's one host synchronisation: the pair count (to size the pair lists) and the range
+    // of the drawn records' depth keys; the depth sort orders only the low bits in which they differ
+    // (the drawn keys share the others; undrawn records emit no pairs).  Its first pass, on key bits
+    // 0-7, needs neither, so it runs on the device while the host waits for the totals.
+    CS_TRY(cudaMemcpyAsync(ctx->host_total, total, sizeof(PreprocessStats), cudaMemcpyDeviceToHost, stream),
+           "read totals");
+    CS_TRY(cudaEventRecord(ctx->totals_ready, stream), "record");
+    if (R > 1) {
+        StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
+        CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, 8, radix_tmp, scan_tmp, &in_b,
+                                stream, s->depth_keys, 0u),
+               "depth sort");
+    }
+    CS_TRY(cudaEventSynchronize(ctx->totals_ready), "synchronize");
+    {
+        const PreprocessStats tot = *reinterpret_cast<const PreprocessStats *>(ctx->host_total);
+        P = tot.pairs;
+        if (P >= 0xffffffffull) {
+            st_code = fail(CS_ERR_ARG, "%llu tile pairs exceed the 32-bit pair index", (unsigned long long)P);
+            goto cleanup;
+        }
+        const uint32_t differ = P ? (~tot.key_min_inv) ^ tot.key_max : 0u;
+        depth_bits = differ ? 32 - __builtin_clz(differ) : 0;
+    }
+    // depth order of the records
+    {
         {
             StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
-            if (depth_bits > 0 && R > 1) {  // the first pass reads the keys rebased, values = indices
-                CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
-                                        scan_tmp, &in_b, stream, s->depth_keys, key_min),
-                       "depth sort");
-            } else {
-                CS_TRY(launch_depth_sort_input(s->depth_keys, R, key_min, sort_keys_a, sort_vals_a, stream),
-                       "sort input");
+            if (R <= 1) {
+                CS_TRY(launch_depth_sort_input(s->depth_keys, R, 0u, sort_keys_a, sort_vals_a, stream), "sort input");
+            } else if (depth_bits > 8) {  // the remaining passes, bits 8 .. depth_bits - 1
+                bool b2 = false;
+                if (in_b) {
+                    CS_TRY(radix_sort_pairs(sort_keys_b, sort_vals_b, sort_keys_a, sort_vals_a, R, depth_bits, radix_tmp,
+                                            scan_tmp, &b2, stream, nullptr, 0u, 8),
+                           "depth sort");
+                    in_b = !b2;
+                } else {
+                    CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
+                                            scan_tmp, &b2, stream, nullptr, 0u, 8),
+                           "depth sort");
+                    in_b = b2;
+                }
             }
         }
         uint32_t *sorted = in_b ? sort_vals_b : sort_vals_a;

@@ -13,6 +13,7 @@ struct cs_context {
     int sm_count = 0;
     cudaMemPool_t pool = nullptr;             // stream-ordered pool for every transient buffer
     unsigned long long *host_total = nullptr; // pinned readback slot for the pair count
+    cudaEvent_t totals_ready = nullptr;       // recorded after the readback of the forward's totals
     // stage profiling: events recorded on the launching stream around every stage
     bool profiling = false;
     struct StageRec {

@@ -98,11 +98,13 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather_idx
 // stable LSD radix sort of (key, value) pairs on the low `bits` key bits.  Buffers a/b alternate;
 // returns in *result_in_b whether the sorted data ended in the b buffers.  With first_keys, the
 // input is (first_keys[i] - first_key_sub, i) instead of the a buffers (first_keys is only read; the
-// sort needs bits > 0 then, since with no pass nothing is written).
+// sort needs bits > bit_begin then, since with no pass nothing is written).  Bits below bit_begin
+// are taken as already sorted by earlier passes.
 size_t radix_tmp_words(int64_t n);
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
-                             cudaStream_t s, const uint32_t *first_keys = nullptr, uint32_t first_key_sub = 0);
+                             cudaStream_t s, const uint32_t *first_keys = nullptr, uint32_t first_key_sub = 0,
+                             int bit_begin = 0);
 
 // the depth sort's input: keys_out[i] = depth_keys[i] - key_min (mod 2^32), vals_out[i] = i.  The
 // drawn records' keys then lie in [0, key_max - key_min]; undrawn records (which emit no pairs)

@@ -479,17 +479,17 @@ size_t radix_tmp_words(int64_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
-                             cudaStream_t s, const uint32_t *first_keys, uint32_t first_key_sub) {
+                             cudaStream_t s, const uint32_t *first_keys, uint32_t first_key_sub, int bit_begin) {
     *result_in_b = false;
-    if (n <= 1 || bits <= 0) return cudaSuccess;
+    if (n <= 1 || bits <= bit_begin) return cudaSuccess;
     const int64_t nb = (n + RADIX_TILE - 1) / RADIX_TILE;
-    const int passes = (bits + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
+    const int passes = (bits - bit_begin + RADIX_MAX_BITS - 1) / RADIX_MAX_BITS;
     uint32_t *hist = tmp;
     uint32_t *offs = tmp + nb * (1 << RADIX_MAX_BITS);
     const uint32_t *kin = first_keys ? first_keys : keys_a;
     const uint32_t *vin = first_keys ? nullptr : vals_a;
     uint32_t *kout = keys_b, *vout = vals_b;
-    int shift = 0;
+    int shift = bit_begin;
     for (int p = 0; p < passes; ++p) {
         const int w = (bits - shift + (passes - p) - 1) / (passes - p);  // spread the bits evenly
         const int64_t nh = (int64_t)(1 << w) * nb;
