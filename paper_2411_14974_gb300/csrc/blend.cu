@@ -400,7 +400,7 @@ __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint3
         any_on = true;
         const float4 c = rec[1];
         const float om = 1.0f - p.alpha;
-        const float inv = __frcp_rn(om);
+        const float inv = rcp(om);  // om >= 1 - alpha_max > 0
         const float Tn = q.Tc[k] * inv;  // transmittance in front of this pair
         const float dalpha = q.G0[k] * (Tn * c.x - q.S0[k] * inv) + q.G1[k] * (Tn * c.y - q.S1[k] * inv) +
                              q.G2[k] * (Tn * c.z - q.S2[k] * inv);
