@@ -3,23 +3,25 @@
 // Forward: one CTA of 256 threads per 16x16 tile, each warp an 8x4 pixel block, each thread one
 // pixel; backward: 128 threads per tile, each warp an 8x8 block, each thread two pixels (rows r
 // and r + 4).  The warps work independently (no CTA barrier).  A warp walks the tile's
-// depth-ordered records 32 at a time: each lane stages one record in the warp's shared-memory
-// slice (128-byte gather), re-expressed relative to the warp's block origin so that every line
-// is two FMAs per pixel, and tests whether any pixel of the block can pass the line pre-test;
-// the warp then evaluates only the records of the resulting ballot.  Per pixel and convex (Eq. S1, S2 and 5):
+// depth-ordered pairs, keeping those whose record's pixel box reaches its block (the block-mask
+// bit carried in the pair key, or the box itself), 32 at a time: each lane stages one record in
+// the warp's shared-memory slice, re-expressed relative to the warp's block origin so that every
+// line is two FMAs per pixel, and tests whether any pixel of the block can pass the line
+// pre-test; the warp then evaluates only the records of the resulting ballot.  Per pixel and
+// convex (Eq. S1, S2 and 5):
 //     s_t  = log2(e) d delta L_t(q)                     (T lines, 2 FMA each)
 //     phi2 = max_t s_t + log2 sum_t 2^(s_t - max)       (= log2(e) phi)
 //     I    = 1 / (1 + 2^(d sigma phi2))                 (= Sigmoid(-d sigma phi))
 //     alpha = min(alpha_max, o I); skip if alpha < tau; C += T alpha c; T *= 1 - alpha
 // A pair whose largest line value already forces alpha < tau is skipped without any
-// transcendental (phi >= max_t s_t).  The whole CTA leaves a batch loop once every pixel's
-// transmittance has dropped below t_min.
+// transcendental (phi >= max_t s_t).  A warp leaves its loop once every pixel of its block has
+// its transmittance below t_min.
 //
 // The backward walks each tile's list in reverse from the last contributor of each pixel,
 // recovering T before a pair as T_after / (1 - alpha), and accumulates d(loss)/d(record) per
-// convex: the 29 per-pixel terms are summed across the warp by a reduce-scatter (31 shuffles,
-// lane l ends with word l) and added to the convex's gradient record by one coalesced atomic
-// instruction per (warp, record).
+// convex: the 3K + 5 per-pixel terms are summed across the warp by a reduce-scatter (16 + 8
+// words, 25 shuffles at K = 6, lane l ends with word l) and added to the convex's gradient record
+// by one coalesced atomic instruction per (warp, record).
 #include "cs_common.cuh"
 
 namespace cs {
