@@ -2,11 +2,12 @@
 // and drawn in order of increasing camera distance to their centres).
 //
 //   1. records sorted by depth key (binary32 bits of the distance, stable, so equal depths keep
-//      increasing record index = convex index within a view);
-//   2. exclusive scan of the per-record tile counts in that order;
-//   3. with several views, a stable pass by view groups the depth-ordered records view by view;
+//      increasing record index = convex index within a view), on the low key bits in which the
+//      drawn records' keys differ only (they share the others; undrawn records emit no pairs);
+//   2. with several views, a stable pass by view groups the depth-ordered records view by view;
+//   3. exclusive scan of the per-record tile counts in that order;
 //   4. each record emits (view << b | tile index within its view, record index) pairs, tiles in
-//      row-major order;
+//      row-major order, with the tile's 8-bit block mask above the view bits when it fits;
 //   5. stable radix sort of the pairs on the b tile bits only: every (view, tile) group ends up
 //      contiguous and in (depth, index) order, as a single sort on (view, tile, depth, index)
 //      would leave it, with no sort passes spent on the view bits;
