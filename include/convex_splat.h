@@ -174,7 +174,8 @@ typedef enum {
     CS_ARR_COUNTS = 3,       /* uint32 [R]: number of tiles the convex covers (the whole range, or the
                                 tiles the exact tile test keeps); 0 if not drawn */
     CS_ARR_PAIR_KEYS = 4,    /* uint32 [P]: view << b | tile index within the view, b = bits of the largest
-                                view's tile count (one view: the tile index) */
+                                view's tile count (one view: the tile index); the device copy also
+                                holds an 8-bit block mask above these bits, which the copy removes */
     CS_ARR_PAIR_VALUES = 5,  /* uint32 [P]: record index (view * N + convex) of each sorted pair */
     CS_ARR_TILE_RANGES = 6,  /* uint32 [tiles][2]: [start, end) of each tile in the pair list; tiles of
                                 all views in view order, row major within a view */

@@ -7,7 +7,8 @@
 //   lines pre-multiplied by log2(e) d^p delta, colour from SH              (Eq. S1, Sec. 3.2)
 // The decisions (visibility, hull, tile range, kept tiles, depth key) are taken in IEEE binary32
 // with a fixed operation order and explicit round-to-nearest intrinsics, so they are
-// reproducible bit for bit.
+// reproducible bit for bit.  The block's records leave through shared memory with coalesced
+// stores, and each block adds its pair count and depth-key range to the launch's totals.
 #include "projection.cuh"
 
 namespace cs {
