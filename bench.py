@@ -539,20 +539,37 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         # roofline of the dominant kernel from the instrumented work counts of one step per view
         dom = max(("blend", "blend_backward"), key=lambda k: breakdown[k])
-        tot = dict(visited=0, lines_visited=0, passed=0, lines_passed=0, contributing=0)
+        fields = ("visited", "lines_visited", "passed", "lines_passed", "contributing")
+        tots = {"blend": dict.fromkeys(fields, 0.0), "blend_backward": dict.fromkeys(fields, 0.0)}
+        n_pairs = n_drawn = 0.0
+        depth_passes = 0.0
         for v in range(len(cams)):
             _, _, st = cs.forward(scene, [cams[v]], settings, keep_state=True, image=image)
-            wc = cs.work_counts(st, dL)["forward" if dom == "blend" else "backward"]
+            wcs = cs.work_counts(st, dL)
+            n_pairs += st.sizes()["pairs"] / len(cams)
+            keys = st.array("depth_keys")[st.array("counts") > 0].astype(np.int64)
+            n_drawn += len(keys) / len(cams)
+            differ = int(keys.max() ^ keys.min()) if len(keys) else 0
+            depth_passes += (-(-differ.bit_length() // 8) if len(keys) > 1 else 0) / len(cams)
             st.release()
-            for k in tot:
-                tot[k] += wc[k] / len(cams)
+            for k in fields:
+                tots["blend"][k] += wcs["forward"][k] / len(cams)
+                tots["blend_backward"][k] += wcs["backward"][k] / len(cams)
+
         # transcendental (MUFU) operations the method needs per evaluated pair: one exp2 per
         # hull line, the log2, the exp2 of the sigmoid and its reciprocal; the backward adds the
         # softmax reciprocal and 1/(1 - alpha) per contributing pair
-        mufu = tot["lines_passed"] + 3 * tot["passed"] + (2 * tot["contributing"] if dom != "blend" else 0)
+        def mufu_ops(t, backward):
+            return t["lines_passed"] + 3 * t["passed"] + (2 * t["contributing"] if backward else 0)
+
         # FP32 pipe instructions: per visited pair 2 FMA + 1 max per line; per evaluated pair one
         # subtract and one add per line plus about 12 for the sigmoid, clamp and compositing
-        fp32 = 3 * tot["lines_visited"] + 2 * tot["lines_passed"] + 12 * tot["passed"]
+        def fp32_ops(t):
+            return 3 * t["lines_visited"] + 2 * t["lines_passed"] + 12 * t["passed"]
+
+        tot = tots[dom]
+        mufu = mufu_ops(tot, dom != "blend")
+        fp32 = fp32_ops(tot)
         sm = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clk.get("sm_max_mhz") or 2070.0
         mufu_peak = sm * 16 * mhz * 1e6 / 1e9   # Gop/s: 16 MUFU results per clock per SM
@@ -584,9 +601,29 @@ def run_ours(args):
         stages["preprocess_backward"] = dict(bound="hbm", bytes=bwd_bytes,
                                              achieved_gbs=bwd_bytes / (breakdown["preprocess_backward"] / 1e3) / 1e9,
                                              peak_gbs=hbm)
-        for st_name in ("preprocess", "preprocess_backward"):
+        # the sorts and the emission against HBM: a radix pass reads the keys twice and the values
+        # once and writes both (20 B per item); the depth sort runs one pass per 8 key bits in which
+        # the drawn records' keys differ, the tile sort one per 8 bits of the tile index (rounded
+        # up), plus reading the sorted keys once for the tile ranges; the count scan reads the
+        # counts twice and writes the offsets, the emission reads 36 B per record (order, count,
+        # offset, rectangle, pixel box) and writes 8 B per pair
+        tile_passes = -(-(((W + 15) // 16) * ((H + 15) // 16) - 1).bit_length() // 8)
+        io_bytes = dict(depth_sort=20 * n_conv * depth_passes,
+                        tile_sort=(20 * tile_passes + 4) * n_pairs,
+                        scan_emit=12 * n_conv + 36 * n_drawn + 8 * n_pairs)
+        for st_name, nbytes in io_bytes.items():
+            stages[st_name] = dict(bound="hbm", bytes=nbytes, achieved_gbs=nbytes / (breakdown[st_name] / 1e3) / 1e9,
+                                   peak_gbs=hbm)
+        for st_name in ("preprocess", "preprocess_backward") + tuple(io_bytes):
             stages[st_name]["frac"] = stages[st_name]["achieved_gbs"] / hbm
-        stages[dom] = dict(bound="alu", mufu_frac=achieved / mufu_peak, fp32_frac=fp32 / t / 1e9 / fp32_peak)
+        for st_name in ("blend", "blend_backward"):
+            tb = breakdown[st_name] / 1e3
+            mf = mufu_ops(tots[st_name], st_name != "blend") / tb / 1e9 / mufu_peak
+            ff = fp32_ops(tots[st_name]) / tb / 1e9 / fp32_peak
+            stages[st_name] = dict(bound="alu", mufu_frac=mf, fp32_frac=ff, frac=max(mf, ff))
+        # end to end: each stage's time at its own bound, summed, over the measured step
+        at_peak_s = sum(stages[k]["frac"] * breakdown[k] / 1e3 for k in stages)
+        stages["end_to_end"] = dict(frac=at_peak_s / (ms_step / 1e3), stages=sorted(k for k in stages))
         out["roofline_stages"] = stages
         # end to end through the host-buffer C-ABI call: scene and cotangent uploaded, image and
         # gradients read back, every step
