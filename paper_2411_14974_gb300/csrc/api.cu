@@ -417,12 +417,12 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
                 bool b2 = false;
                 if (in_b) {
                     CS_TRY(radix_sort_pairs(sort_keys_b, sort_vals_b, sort_keys_a, sort_vals_a, R, depth_bits, radix_tmp,
-                                            scan_tmp, &b2, stream, nullptr, 0u, 8),
+                                            scan_tmp, &b2, stream, nullptr, 0u, 8, true),
                            "depth sort");
                     in_b = !b2;
                 } else {
                     CS_TRY(radix_sort_pairs(sort_keys_a, sort_vals_a, sort_keys_b, sort_vals_b, R, depth_bits, radix_tmp,
-                                            scan_tmp, &b2, stream, nullptr, 0u, 8),
+                                            scan_tmp, &b2, stream, nullptr, 0u, 8, true),
                            "depth sort");
                     in_b = b2;
                 }
@@ -434,13 +434,16 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             StageTimer tv(ctx, CS_STAGE_DEPTH_SORT, stream);
             uint32_t *vk = in_b ? sort_keys_b : sort_keys_a, *vk2 = in_b ? sort_keys_a : sort_keys_b;
             uint32_t *vv2 = in_b ? sort_vals_a : sort_vals_b;
-            CS_TRY(launch_view_keys(s->views_dev, V, sorted, R, vk, stream), "view keys");
+            CS_TRY(launch_view_keys(s->views_dev, V, sorted, R, vk, stream, true), "view keys");
             bool vb = false;
-            CS_TRY(radix_sort_pairs(vk, sorted, vk2, vv2, R, view_bits, radix_tmp, scan_tmp, &vb, stream), "view sort");
+            CS_TRY(radix_sort_pairs(vk, sorted, vk2, vv2, R, view_bits, radix_tmp, scan_tmp, &vb, stream, nullptr, 0u, 0,
+                                    true),
+                   "view sort");
             if (vb) sorted = vv2;
         }
         StageTimer tm(ctx, CS_STAGE_SCAN_EMIT, stream);
-        CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, nullptr, scan_tmp, stream), "scan");
+        // the depth (or view) sort's last kernel precedes it
+        CS_TRY(launch_exclusive_scan(s->counts, sorted, offsets, R, nullptr, scan_tmp, stream, R > 0), "scan");
         s->n_pairs = (int64_t)P;
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_keys, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");

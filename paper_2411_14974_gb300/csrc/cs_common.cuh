@@ -91,9 +91,12 @@ cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, i
 
 // device-wide exclusive scan of n uint32 values (optionally gathered through idx); writes the
 // 64-bit total to *total_dev.  tmp must hold scan_tmp_words(n) uint64 words.
+// pdl_first (here and below): the stream operation before the call is a kernel of the sort chain,
+// so the first launch may be a programmatic dependent of it.
 size_t scan_tmp_words(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather_idx, uint32_t *out, int64_t n,
-                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s);
+                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s,
+                                  bool pdl_first = false);
 
 // stable LSD radix sort of (key, value) pairs on the low `bits` key bits.  Buffers a/b alternate;
 // returns in *result_in_b whether the sorted data ended in the b buffers.  With first_keys, the
@@ -104,7 +107,7 @@ size_t radix_tmp_words(int64_t n);
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
                              cudaStream_t s, const uint32_t *first_keys = nullptr, uint32_t first_key_sub = 0,
-                             int bit_begin = 0);
+                             int bit_begin = 0, bool pdl_first = false);
 
 // the depth sort's input: keys_out[i] = depth_keys[i] - key_min (mod 2^32), vals_out[i] = i.  The
 // drawn records' keys then lie in [0, key_max - key_min]; undrawn records (which emit no pairs)
@@ -113,7 +116,7 @@ cudaError_t launch_depth_sort_input(const uint32_t *depth_keys, int64_t n, uint3
                                     uint32_t *vals_out, cudaStream_t s);
 // keys[j] = view index of record sorted_records[j]
 cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
-                             uint32_t *keys, cudaStream_t s);
+                             uint32_t *keys, cudaStream_t s, bool pdl = false);
 // pair key = view << local_bits | tile index within the view, and, when mask_shift > 0, the pair's
 // block mask << mask_shift: bit 2 q + c set when the record's pixel box holds a pixel centre of the
 // tile's 8x4 block in column c, row q (the blocks of the forward blend's warps).  The tile sort

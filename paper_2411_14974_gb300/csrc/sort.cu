@@ -16,6 +16,8 @@
 // The radix sort is a three-kernel LSD sort (digit histogram per tile of 4096 keys, scan of the
 // digit-major histogram, stable scatter).  Ranks inside a block come from warp-level key matching
 // (__match_any_sync) over warp-striped runs of keys, so the scatter is stable.
+#include <utility>
+
 #include "cs_common.cuh"
 #include "cs_spec_math.cuh"
 
@@ -38,6 +40,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Kernels of the sort chain may be launched as programmatic dependents of the chain kernel before
+// them: each waits here for that grid to complete (its results, and by the same wait in every
+// chain kernel those of all earlier ones, are then visible), and at once lets its own dependent
+// be scheduled, so that launches overlap the tail of the previous kernel.
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // ---- scan -----------------------------------------------------------------------------------
@@ -77,6 +88,7 @@ __device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *__restrict__ in,
                                                               const uint32_t *__restrict__ gather, int64_t n,
                                                               unsigned long long *__restrict__ partial) {
+    chain_enter();
     __shared__ unsigned long long sh[32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     unsigned long long s = 0;
@@ -89,6 +101,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t *__
 
 __global__ void __launch_bounds__(SPINE_THREADS) k_scan_spine(unsigned long long *__restrict__ partial, int64_t nb,
                                                               unsigned long long *__restrict__ total_out) {
+    chain_enter();
     __shared__ unsigned long long sh[32];
     unsigned long long carry = 0;
     for (int64_t b0 = 0; b0 < nb; b0 += SPINE_THREADS) {
@@ -110,6 +123,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__re
                                                             const unsigned long long *__restrict__ partial,
                                                             uint32_t *__restrict__ out,
                                                             unsigned long long *__restrict__ total_out) {
+    chain_enter();
     __shared__ unsigned long long sh[32];
     unsigned long long prefix;
     if (INLINE) {
@@ -143,6 +157,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t *__re
 __global__ void __launch_bounds__(RADIX_THREADS) k_radix_upsweep(const uint32_t *__restrict__ keys, int64_t n,
                                                                  int shift, int nbits, uint32_t key_sub,
                                                                  uint32_t *__restrict__ hist, int64_t nblocks) {
+    chain_enter();
     __shared__ uint32_t cnt[RADIX_WARPS][1 << RADIX_MAX_BITS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t nbins = 1u << nbits, mask = nbins - 1;
@@ -198,6 +213,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
                                                                  const uint32_t *__restrict__ offsets,
                                                                  int64_t nblocks, uint32_t *__restrict__ keys_out,
                                                                  uint32_t *__restrict__ vals_out) {
+    chain_enter();
     // ranks are stable: warp-striped runs of 32 keys in index order, counted per warp and digit;
     // the block's keys are then laid out by digit in shared memory so that each digit's run is
     // written to its global bucket with consecutive addresses
@@ -297,6 +313,7 @@ __device__ __forceinline__ int view_of_record(const ViewDesc *__restrict__ views
 
 __global__ void k_view_keys(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
                             int64_t n, uint32_t *__restrict__ keys) {
+    chain_enter();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) keys[j] = (uint32_t)view_of_record(views, n_views, sorted[j]);
 }
@@ -454,23 +471,46 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, const Vie
 
 size_t scan_tmp_words(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 1; }
 
+// Launches a chain kernel; with pdl, as a programmatic dependent of the kernel before it in the
+// stream (only when that stream operation is a chain kernel: the kernel's wait then covers it).
+template <typename... Exp, typename... Act>
+static cudaError_t launch_chain(bool pdl, void (*kernel)(Exp...), unsigned grid, unsigned block, cudaStream_t s,
+                                Act &&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Act>(args)...);
+}
+
 cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather, uint32_t *out, int64_t n,
-                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s) {
+                                  unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s,
+                                  bool pdl_first) {
     if (n <= 0) {
         if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp);
+    cudaError_t e = launch_chain(pdl_first, k_scan_reduce, (unsigned)nb, SCAN_THREADS, s, in, gather, n, tmp);
+    if (e != cudaSuccess) return e;
     if (nb <= SCAN_INLINE_BLOCKS) {
-        k_scan_down<true><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out, total_dev);
+        e = launch_chain(true, k_scan_down<true>, (unsigned)nb, SCAN_THREADS, s, in, gather, n,
+                         (const unsigned long long *)tmp, out, total_dev);
         count_launches(2);
     } else {
-        k_scan_spine<<<1, SPINE_THREADS, 0, s>>>(tmp, nb, total_dev);
-        k_scan_down<false><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, gather, n, tmp, out, nullptr);
+        e = launch_chain(true, k_scan_spine, 1u, SPINE_THREADS, s, tmp, nb, total_dev);
+        if (e == cudaSuccess)
+            e = launch_chain(true, k_scan_down<false>, (unsigned)nb, SCAN_THREADS, s, in, gather, n,
+                             (const unsigned long long *)tmp, out, (unsigned long long *)nullptr);
         count_launches(3);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 size_t radix_tmp_words(int64_t n) {
@@ -480,7 +520,8 @@ size_t radix_tmp_words(int64_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, int64_t n,
                              int bits, uint32_t *tmp, unsigned long long *scan_tmp, bool *result_in_b,
-                             cudaStream_t s, const uint32_t *first_keys, uint32_t first_key_sub, int bit_begin) {
+                             cudaStream_t s, const uint32_t *first_keys, uint32_t first_key_sub, int bit_begin,
+                             bool pdl_first) {
     *result_in_b = false;
     if (n <= 1 || bits <= bit_begin) return cudaSuccess;
     const int64_t nb = (n + RADIX_TILE - 1) / RADIX_TILE;
@@ -495,10 +536,13 @@ cudaError_t radix_sort_pairs(uint32_t *keys_a, uint32_t *vals_a, uint32_t *keys_
         const int w = (bits - shift + (passes - p) - 1) / (passes - p);  // spread the bits evenly
         const int64_t nh = (int64_t)(1 << w) * nb;
         const uint32_t sub = (p == 0 && first_keys) ? first_key_sub : 0u;
-        k_radix_upsweep<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, n, shift, w, sub, hist, nb);
-        cudaError_t e = launch_exclusive_scan(hist, nullptr, offs, nh, nullptr, scan_tmp, s);
+        cudaError_t e = launch_chain(p > 0 || pdl_first, k_radix_upsweep, (unsigned)nb, RADIX_THREADS, s, kin, n, shift,
+                                     w, sub, hist, nb);
+        if (e == cudaSuccess) e = launch_exclusive_scan(hist, nullptr, offs, nh, nullptr, scan_tmp, s, true);
+        if (e == cudaSuccess)
+            e = launch_chain(true, k_radix_scatter, (unsigned)nb, RADIX_THREADS, s, kin, vin, n, shift, w, sub,
+                             (const uint32_t *)offs, nb, kout, vout);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)nb, RADIX_THREADS, 0, s>>>(kin, vin, n, shift, w, sub, offs, nb, kout, vout);
         count_launches(2);
         shift += w;
         // the next pass reads what this one wrote and writes the other buffer (never first_keys)
@@ -521,11 +565,12 @@ cudaError_t launch_depth_sort_input(const uint32_t *depth_keys, int64_t n, uint3
 }
 
 cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records, int64_t n,
-                             uint32_t *keys, cudaStream_t s) {
+                             uint32_t *keys, cudaStream_t s, bool pdl) {
     if (n <= 0) return cudaSuccess;
-    k_view_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, n, keys);
+    const cudaError_t e = launch_chain(pdl, k_view_keys, (unsigned)((n + 255) / 256), 256u, s, views_dev, n_views,
+                                       sorted_records, n, keys);
     count_launches(1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
