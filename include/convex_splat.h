@@ -34,7 +34,8 @@
  *     cs_last_error() (thread-local) describes the cause.  Asynchronous device errors are
  *     reported by the next call that synchronises.
  *   - The stream argument is a cudaStream_t (0 = legacy default stream).  Work is enqueued on it;
- *     cs_forward synchronises the stream once (to size the tile-pair buffers).
+ *     cs_forward waits once on the host, for the preprocess's totals (the tile-pair count that sizes
+ *     the pair buffers, and the range of the depth keys); work it has already queued keeps running.
  */
 #ifndef CONVEX_SPLAT_H
 #define CONVEX_SPLAT_H
