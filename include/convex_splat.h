@@ -132,8 +132,9 @@ void cs_default_settings(cs_settings *s);
 const char *cs_last_error(void);
 
 /* Create a context on CUDA device `device`.  The context owns a stream-ordered memory pool for
-   the transient buffers of every call made with it.  Returns CS_ERR_CUDA if the device cannot be
-   used (no GPU, wrong architecture). */
+   the transient buffers of every call made with it, and the forward's readback slot, so calls on
+   one context must not overlap: use one context per host thread (the serving loop makes its own).
+   Returns CS_ERR_CUDA if the device cannot be used (no GPU, wrong architecture). */
 cs_status cs_context_create(int32_t device, cs_context **out);
 void cs_context_destroy(cs_context *ctx);
 
