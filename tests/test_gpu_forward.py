@@ -334,3 +334,31 @@ def test_depth_keys_over_a_wide_range():
     keys = disc["depth_bits"][disc["visible"] == 1].astype(np.int64)
     assert len(keys) > n // 2 and (int(keys.max()) ^ int(keys.min())) >> 24
     check_pairs(state, [disc], [cam])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_work_counts_against_the_oracle(seed):
+    """Evaluations counted on the GPU (the instrumented blend kernels) against the oracle on the
+    1000-convex 128 x 128 scenes: every pixel is counted once; the backward's contributing pairs
+    (alpha >= tau up to each pixel's last contributor, the pairs the forward composited) equal the
+    oracle's composited pairs up to the pixels whose cut-off decisions sit within their error
+    bands; the forward, which may evaluate a record past a pixel's termination, counts no fewer."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc, cams = syn.workload("blob1k_128", seed=seed)
+    cam = cams[0]
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    _, _, st = cs.forward(t, [cam], cs.Settings(), keep_state=True)
+    wc = cs.work_counts(st, torch.ones((1, 3, cam.height, cam.width), device=dev))
+    torch.cuda.synchronize()
+    st.release()
+    ref = oracle.render_image(sc, cam, oracle.settings())
+    nc = ref["n_contrib"].astype(np.int64)
+    flagged = ref["flags"] != 0
+    total, slack = int(nc.sum()), int(nc[flagged].sum() + flagged.sum())
+    f, b = wc["forward"], wc["backward"]
+    assert f["pixels"] == b["pixels"] == cam.width * cam.height
+    assert abs(b["contributing"] - total) <= slack, (b["contributing"], total, slack)
+    assert f["contributing"] >= b["contributing"]
+    assert f["visited"] >= f["passed"] >= f["contributing"] and f["lines_visited"] >= f["lines_passed"]
