@@ -8,6 +8,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import math
+import threading
 from typing import Optional, Sequence
 
 import numpy as np
@@ -65,7 +66,9 @@ def cameras_array(cams: Sequence) -> ctypes.Array:
 
 
 class Context:
-    """Per-device library context (owns the stream-ordered memory pool of transient buffers)."""
+    """Library context on one device (owns the stream-ordered memory pool of transient buffers and
+    the forward's readback slot).  Calls on one context must not overlap, and ctypes releases the
+    interpreter lock during a call, so `get` gives each host thread its own context."""
     _by_device: dict = {}
 
     def __init__(self, device: int = 0):
@@ -76,9 +79,10 @@ class Context:
 
     @classmethod
     def get(cls, device: int = 0) -> "Context":
-        if device not in cls._by_device:
-            cls._by_device[device] = Context(device)
-        return cls._by_device[device]
+        key = (int(device), threading.get_ident())
+        if key not in cls._by_device:
+            cls._by_device[key] = Context(device)
+        return cls._by_device[key]
 
     def __del__(self):
         try:
