@@ -52,7 +52,7 @@ class OrcSettings(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float),
                 ("q_binary32", ctypes.c_int32), ("perturb_ulps", ctypes.c_float), ("line_rel", ctypes.c_float),
-                ("tile_test", ctypes.c_int32)]
+                ("tile_test", ctypes.c_int32), ("line_f32", ctypes.c_int32)]
 
 
 _lib = None
@@ -115,7 +115,8 @@ def camera(cam) -> OrcCamera:
 
 
 def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), dist_mode=0,
-             dist_power=1.0, q_binary32=False, perturb_ulps=4.0, line_rel=0.0, tile_test=0) -> OrcSettings:
+             dist_power=1.0, q_binary32=False, perturb_ulps=4.0, line_rel=0.0, tile_test=0,
+             line_f32=False) -> OrcSettings:
     """Method settings plus oracle-only knobs (no counterpart in the method).
 
     q_binary32: build the hull lines from the binary32 projected points the hull was decided on
@@ -124,7 +125,10 @@ def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), di
     Error model for the conditioning bound ``sens``, the decision bands and the probes:
       line_rel > 0: every line value may be off by line_rel (|q - a|_1 + |a - v_t|_1 + 32 + |L_t|)
                     pixels (binary32 evaluation relative to the anchor vertex a);
-      otherwise:    every hull vertex may move by perturb_ulps binary32 ulps."""
+      otherwise:    every hull vertex may move by perturb_ulps binary32 ulps.
+    line_f32: evaluate every line value in binary32 from the record form of the discrete
+    specification (anchored lines scaled by log2(e) d^p delta, re-based to the pixel's 8 x 4 block
+    origin, fused multiply-adds), the rest in binary64; used only to check the line_rel model."""
     s = OrcSettings()
     s.tau, s.alpha_max, s.t_min = float(tau), float(alpha_max), float(t_min)
     for i in range(3):
@@ -132,6 +136,7 @@ def settings(tau=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, bg=(0.0, 0.0, 0.0), di
     s.dist_mode, s.dist_power = int(dist_mode), float(dist_power)
     s.q_binary32, s.perturb_ulps, s.line_rel = int(bool(q_binary32)), float(perturb_ulps), float(line_rel)
     s.tile_test = int(tile_test)
+    s.line_f32 = int(bool(line_f32))
     return s
 
 

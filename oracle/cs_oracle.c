@@ -76,6 +76,13 @@ typedef struct {
        otherwise the vertex-motion model (every hull vertex moves by perturb_ulps ulps) is used. */
     float line_rel;
     int32_t tile_test; /* the method's exact tile test (cs_settings.tile_test) */
+    /* line_f32 = 1 replaces every line value by its binary32 evaluation in record form (the lines
+       kappa n_t and kappa n_t . (a - v_t) of the discrete specification, kappa = log2(e) d^p delta,
+       evaluated at the pixel after re-basing them, with fused multiply-adds, to the origin of the
+       pixel's 8 x 4 block), converted back to pixels with the binary64 d^p delta.  This is how a
+       binary32 renderer built on that record evaluates the lines; the mode exists to check the
+       line_rel error model against it (conditioning tests only). */
+    int32_t line_f32;
 } orc_settings;
 
 /* flags reported per pixel by the continuous render */
@@ -638,6 +645,9 @@ typedef struct {
     double o;
     double rgb[3], raw[3];
     double r_pre; /* max_t L_t > r_pre guarantees alpha < tau - ORC_ALPHA_BAND */
+    /* record-form binary32 lines and anchor (line_f32 mode), and ln 2 / (d^p delta) */
+    float rA[ORC_KMAX], rB[ORC_KMAX], rC[ORC_KMAX], rax, ray;
+    double s_to_px;
 } orc_convex;
 
 static uint64_t splitmix64(uint64_t x) {
@@ -733,6 +743,14 @@ static void continuous_convex(const float *P, int K, float delta, float sigma, f
         cv->raw[ch] = s;
         cv->rgb[ch] = s > 0.0 ? s : 0.0;
     }
+    for (int i = 0; i < dsc->T; i++) {
+        cv->rA[i] = dsc->lA[i];
+        cv->rB[i] = dsc->lB[i];
+        cv->rC[i] = dsc->lC[i];
+    }
+    cv->rax = dsc->ax;
+    cv->ray = dsc->ay;
+    cv->s_to_px = 0.6931471805599453 / cv->dp;
     double tl = (double)st->tau - ORC_ALPHA_BAND;
     if (tl > 0.0 && cv->o > tl)
         cv->r_pre = log(cv->o / tl - 1.0) / (cv->sp * cv->dp) * (1.0 + 1e-9) + 1e-9;
@@ -822,13 +840,27 @@ static double alpha_sensitivity(const orc_convex *cv, const orc_settings *st, do
     return cv->o * I * (1.0 - I) * cv->sp * dphi + 1e-7;
 }
 
+/* line_f32 mode: line t at the pixel whose centre is (x, y), evaluated in binary32 from the
+   record form: re-based to the pixel's 8 x 4 block origin (ox, oy) as
+   C' = A (ox - a.x) + B (oy - a.y) + C, then s = A lx + B ly + C' at the pixel's offset (lx, ly)
+   from that origin, each a fused multiply-add; returned in pixels (s ln 2 / (d^p delta)). */
+static double line_record_f32(const orc_convex *cv, int t, double x, double y) {
+    const int px = (int)floor(x), py = (int)floor(y);
+    const int bx = px - px % 8, by = py - py % 4;
+    const float offx = (float)bx - cv->rax, offy = (float)by - cv->ray;
+    const float cp = fmaf(cv->rA[t], offx, fmaf(cv->rB[t], offy, cv->rC[t]));
+    const float lx = (float)(px - bx) + 0.5f, ly = (float)(py - by) + 0.5f;
+    const float s = fmaf(cv->rA[t], lx, fmaf(cv->rB[t], ly, cp));
+    return (double)s * cv->s_to_px;
+}
+
 /* evaluate the smooth indicator of convex cv at pixel position (x, y); returns 0 when the pair
    is provably below tau - band (no exponentials needed), else fills phi, I and the L_t. */
 static int indicator(const orc_convex *cv, const orc_settings *st, uint64_t probe, int64_t id, double x, double y,
                      double L[ORC_KMAX], double *phi, double *I) {
     double Lmax = -INFINITY;
     for (int t = 0; t < cv->T; t++) {
-        L[t] = cv->n[t][0] * x + cv->n[t][1] * y + cv->c0[t];
+        L[t] = st->line_f32 ? line_record_f32(cv, t, x, y) : cv->n[t][0] * x + cv->n[t][1] * y + cv->c0[t];
         if (probe && st->line_rel > 0.0f) { /* conditioning probe of the line-evaluation model */
             uint64_t h = splitmix64(probe ^ (uint64_t)(id * 16 + t) * 0x9e3779b97f4a7c15ull);
             L[t] += ((h & 1) ? 1.0 : -1.0) * line_error(cv, st, x, y, t, L[t]);

@@ -150,8 +150,9 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     if (e == cudaSuccess) e = launch_exclusive_scan(counts, sorted, offsets, R, nullptr, scan_tmp, stream);
     const int local_bits = bits_for(tiles);
     const int mask_shift = local_bits + BLOCK_MASK_BITS <= 32 ? local_bits : 0;
-    e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, bboxes, R, local_bits,
-                          mask_shift, pk, pv, stream);
+    if (e == cudaSuccess)
+        e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, bboxes, R, local_bits,
+                              mask_shift, pk, pv, stream);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);
     const uint32_t *keys = in_b ? pk2 : pk;

@@ -50,3 +50,23 @@ def test_no_gpu_calls_on_cpu(library):
         code = lib.cs_context_create(0, ctypes.byref(h))
         assert code != 0 and not h.value
         assert len(lib.cs_last_error()) > 0
+
+
+def test_static_forward_reports_a_failed_runtime_call_on_cpu(library):
+    """cs_forward_static with valid arguments but no usable device: the first runtime call fails
+    on the host and the entry point returns that failure with a message (no crash, no CS_OK)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a usable GPU")
+    lib = _binding.lib()
+    buf = (ctypes.c_float * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    sc = _binding.CsScene(points=p, delta=p, sigma=p, opacity=p, sh=p, n=1, k=3, sh_degree=0, activation=0,
+                          storage=0)
+    cam = _binding.CsCamera(width=16, height=16, fx=10.0, fy=10.0, cx=8.0, cy=8.0, z_near=0.2)
+    cam.R[0] = cam.R[4] = cam.R[8] = 1.0
+    s = _binding.CsSettings()
+    lib.cs_default_settings(ctypes.byref(s))
+    code = lib.cs_forward_static(ctypes.byref(sc), ctypes.byref(cam), ctypes.byref(s), p, p, None)
+    assert code == 2  # CS_ERR_CUDA
+    assert len(lib.cs_last_error()) > 0

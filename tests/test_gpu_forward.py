@@ -1,9 +1,14 @@
 """GPU forward parity with the oracle, through the C ABI.
 
 Bit-exact: visibility, hull vertex indices, tile ranges, depth keys and the sorted tile-pair lists
-(Sec. 3.2).  Within 1e-4 per channel: the images (Eq. 5), outside the conditioning mask (pixels
-whose binary64 value moves by more than 2.5e-5 when the projected points move by 4 binary32
-ulps, or where a cut-off decision is within its band).
+(Sec. 3.2).  Within 1e-4 per channel: the images (Eq. 5), outside a conditioning mask, under two
+protocols.  (1) Against the oracle with hull lines built from the binary32 projected points
+(q_binary32): pixels whose first-order bound of the change under the binary32 line-evaluation
+error model exceeds 2.5e-5, or where a cut-off decision is within its band, are excluded (the
+model is checked against the binary32 record-form lines in tests/test_oracle_conditioning.py).
+(2) Against the binary64-projection oracle: pixels whose value moves by more than 2.5e-5 when the
+projected points move by 4 binary32 ulps (four seeded sign patterns), or where a cut-off decision
+is within its band, are excluded.  Every test bounds the excluded fraction.
 """
 import numpy as np
 import pytest
@@ -112,7 +117,7 @@ def test_exact_tile_test_parity(scene):
         assert (area[vis] > 8).sum() > 100  # the warp-cooperative path runs
     check_pairs(state, [disc], [cam])
     ref, ill = P.oracle_reference(sc, cam, tile_test=1)
-    check_image(img[0], ref, ill, max_ill=0.08)
+    check_image(img[0], ref, ill, max_ill={"blob": 0.03, "surface": 0.06, "clustered": 0.04}[scene])
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -137,6 +142,45 @@ def test_well_conditioned_needs_no_mask():
     assert d[~flag].max() <= P.IMAGE_TOL
 
 
+def _fp64_protocol_reference(sc, cam, **kw):
+    """The second parity protocol: the oracle's binary64 projection (no binary32 vertices), and a
+    mask of the pixels whose binary64 value moves by more than COND_TOL when every projected
+    coordinate moves by 4 binary32 ulps (four seeded sign patterns), or where a cut-off decision
+    lies within its band."""
+    st = oracle.settings(perturb_ulps=4.0, **kw)
+    r0 = oracle.render_image(sc, cam, st)
+    moved = np.zeros(r0["image"].shape[1:])
+    for seed in (1, 2, 3, 4):
+        moved = np.maximum(moved, np.abs(oracle.render_image(sc, cam, st, perturb_seed=seed)["image"] -
+                                         r0["image"]).max(0))
+    flagged = (r0["flags"] & 3) != 0
+    return r0, (moved > P.COND_TOL) | flagged, flagged
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_blob1k_128_image_binary64_projection(seed):
+    """Against the binary64-projection oracle with the 4-ulp vertex probe as the mask."""
+    sc, cams = syn.workload("blob1k_128", seed=seed)
+    ref, ill, _ = _fp64_protocol_reference(sc, cams[0])
+    img, tf, _, _ = P.gpu_render(sc, cams, keep_state=False)
+    check_image(img[0], ref, ill, max_ill=0.02)
+    assert np.abs(tf[0] - ref["t_final"])[~ill].max() <= P.IMAGE_TOL
+
+
+def test_well_conditioned_binary64_projection_needs_no_probe_mask():
+    """sigma in [0.01, 0.3], delta in [0.5, 5]: against the binary64-projection oracle with only
+    the cut-off decisions within their bands excluded (no vertex-probe mask)."""
+    sc, cams = syn.workload("blob1k_128", seed=3)
+    rng = np.random.default_rng(3)
+    sc.sigma = np.exp(rng.uniform(np.log(0.01), np.log(0.3), sc.n)).astype(np.float32)
+    sc.delta = np.exp(rng.uniform(np.log(0.5), np.log(5.0), sc.n)).astype(np.float32)
+    ref, _, flagged = _fp64_protocol_reference(sc, cams[0])
+    img, _, _, _ = P.gpu_render(sc, cams, keep_state=False)
+    assert flagged.mean() < 0.02
+    d = np.abs(img[0] - ref["image"]).max(0)
+    assert d[~flagged].max() <= P.IMAGE_TOL
+
+
 @pytest.mark.parametrize("w,h", [(100, 75), (17, 33), (1, 1), (129, 16)])
 def test_ragged_sizes(w, h):
     sc, _ = syn.workload("blob1k_128", seed=4)
@@ -145,7 +189,7 @@ def test_ragged_sizes(w, h):
     img, _, state, _ = P.gpu_render(sc, [cam])
     disc = check_discrete(state, sc, cam)
     check_pairs(state, [disc], [cam])
-    check_image(img[0], ref, ill, max_ill=0.05 if w * h > 64 else 1.0)
+    check_image(img[0], ref, ill, max_ill=0.04 if w * h > 64 else 1.0)
 
 
 @pytest.mark.parametrize("k,deg", [(3, 1), (4, 2), (5, 3), (7, 0), (8, 3)])
@@ -158,7 +202,7 @@ def test_points_per_convex_and_sh_degree(k, deg):
     check_pairs(state, [disc], [cam])
     # small sharp convexes at 96x80, and projected triangles that are often thin slivers: a larger
     # share of pixels is ill-conditioned than in the 128x128 blob scenes
-    check_image(img[0], ref, ill, max_ill={3: 0.08, 4: 0.06}.get(k, 0.06))
+    check_image(img[0], ref, ill, max_ill={3: 0.04, 4: 0.05, 5: 0.06, 7: 0.04, 8: 0.07}[k])
 
 
 @pytest.mark.parametrize("kw", [dict(dist_power=0.0), dict(dist_power=0.5), dict(dist_power=2.0),
@@ -173,7 +217,7 @@ def test_settings_variants(kw):
     img, _, state, _ = P.gpu_render(sc, cams, **kw)
     disc = check_discrete(state, sc, cams[0], **kw)
     check_pairs(state, [disc], cams)
-    check_image(img[0], ref, ill, max_ill=0.05)
+    check_image(img[0], ref, ill, max_ill=0.04)
 
 
 def test_tau_zero_full_screen_ranges():
@@ -260,7 +304,7 @@ def test_light_16bit_storage(dtype_name):
         disc = check_discrete(state, wide, cam)
         check_pairs(state, [disc], [cam])
         ref, ill = P.oracle_reference(wide, cam)
-        check_image(img[0].cpu().numpy().astype(np.float64), ref, ill, max_ill=0.08)
+        check_image(img[0].cpu().numpy().astype(np.float64), ref, ill, max_ill=0.05)
         state.release()
 
 
@@ -284,7 +328,7 @@ def test_surface_scene_image_sh3():
     img, _, state, _ = P.gpu_render(sc, [cam])
     check_discrete(state, sc, cam)
     # sub-pixel, very sharp convexes at this resolution: more alpha ~ tau crossings
-    check_image(img[0], ref, ill, max_ill=0.06)
+    check_image(img[0], ref, ill, max_ill=0.045)
 
 
 def test_square_worked_example_on_gpu():

@@ -61,4 +61,4 @@ def test_fullsize_sampled_pixel_gradient(workload):
     ref = oracle.backward_pixels(sc, cam, st, pix, w.astype(np.float32).astype(np.float64))
     refp = [oracle.backward_pixels(sc, cam, st, pix, w.astype(np.float32).astype(np.float64), perturb_seed=s)
             for s in (1, 2)]
-    compare(got, ref, refp, max_excluded=0.15)
+    compare(got, ref, refp)
