@@ -54,7 +54,7 @@ typedef enum {
     CS_ERR_NOMEM = 3,    /* device or host allocation failed */
     CS_ERR_BUDGET = 4,   /* a serving request does not fit the memory budget */
     CS_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
-    CS_ERR_DEVICE = 6,   /* a kernel reported an error through the device status word */
+    CS_ERR_DEVICE = 6,   /* checked builds only: a kernel's index test failed (status word) */
     CS_ERR_STATE = 7     /* object used in the wrong state (e.g. released, unknown id) */
 } cs_status;
 
@@ -317,12 +317,14 @@ cs_status cs_refine(cs_context *ctx, int64_t n, int32_t k, int32_t sh_degree, co
    A server keeps several scenes resident (device buffers owned by the caller, registered with
    cs_server_add_scene) and renders view requests of mixed resolution.  A worker thread admits
    queued requests in arrival order into a batch of at most max_batch views, as long as the
-   estimated transient memory of the batch plus the batches still on the GPU fits the memory
+   estimated transient memory of the batch plus what the batches still on the GPU hold (their
+   estimates, or the server's memory pool's real usage when that is more) fits the memory
    budget; requests that arrive while earlier batches are on the GPU join the next batch as soon
-   as memory frees up.  A batch is binned and sorted as one (the view index lives in the tile
-   key) and blended by one kernel launch over the (view, tile) pairs of all its views; batches
-   alternate between two streams, so the preprocess and sorts of one overlap the blend of the
-   previous one.  Each view's image is identical to rendering it alone with cs_forward.
+   as memory frees up.  A batch is preprocessed, binned and sorted as one (the view index lives in
+   the tile key), then blended view by view, cheapest view first; each request completes as soon
+   as its own view's blend has run.  Batches alternate between two streams, so the preprocess and
+   sorts of one overlap the blends of the previous one.  Each view's image is identical to
+   rendering it alone with cs_forward.
    Images are written to caller-owned device buffers [3][H][W] that must stay alive until the
    request's completion has been polled.  All calls are thread-safe. */
 typedef struct cs_server cs_server;
@@ -336,7 +338,7 @@ typedef struct {
     double latency_ms;    /* submit -> image complete on the device */
 } cs_completion;
 
-/* memory_budget_bytes bounds the estimated transient device memory of admitted batches;
+/* memory_budget_bytes bounds the transient device memory of admitted batches (see above);
    1 <= max_batch <= 1024.  settings apply to every request. */
 cs_status cs_server_create(int32_t device, size_t memory_budget_bytes, int32_t max_batch, const cs_settings *settings,
                            cs_server **out);
@@ -355,8 +357,10 @@ cs_status cs_server_submit(cs_server *srv, int32_t scene_id, const cs_camera *ca
 /* Moves up to max completions into out (oldest first); waits up to wait_ms milliseconds for the
    first one when none is ready (0 = do not wait). */
 cs_status cs_server_poll(cs_server *srv, cs_completion *out, int32_t max, int32_t *n_out, int32_t wait_ms);
-/* Counters: [0] requests completed, [1] batches run, [2] largest batch, [3] peak estimated bytes
-   in flight, [4] requests queued now, [5] requests on the GPU now. */
+/* Counters (stats: 7 values): [0] requests completed, [1] batches run, [2] largest batch,
+   [3] peak estimated bytes in flight, [4] requests queued now, [5] requests on the GPU now,
+   [6] peak bytes the server's memory pool really held for batches (its high-water mark since
+   cs_server_create). */
 cs_status cs_server_stats(cs_server *srv, uint64_t *stats);
 
 /* ---- instrumentation (no counterpart in the paper) ------------------------------------------ */
@@ -381,6 +385,28 @@ cs_status cs_profile_enable(cs_context *ctx, int32_t on);
 cs_status cs_profile_read(cs_context *ctx, double *ms, int64_t *launches);
 /* Total number of kernels this library has launched in the process (monotonic). */
 uint64_t cs_kernel_launch_count(void);
+
+/* Checked builds (no counterpart in the paper).  The library built with CS_CHECKED=1 tests, in
+   its kernels, every index that an inconsistent upstream value could send outside its buffer (a
+   tile's pair range, a pair's record index, a record's hull count, an emitted pair slot, a tile
+   index, a radix-sort destination); a failed test skips or clamps that access and sets a bit of a
+   device status word, never traps.  cs_forward, cs_backward and cs_forward_static then synchronise
+   their stream, read and clear the words and return CS_ERR_DEVICE, naming the bits.  Every
+   transient buffer is handed out filled with 0xff bytes (NaN as float), so that a read before a
+   write changes the results.  The status words are per process and device: concurrent calls share
+   them.  Production builds compile all of this out and never return CS_ERR_DEVICE.
+   cs_debug_set_pair_value overwrites entry `index` of a forward state's sorted pair values (the
+   record each tile pair refers to), so that a test can hand the backward an inconsistent pair list
+   for the checks to catch; production builds return CS_ERR_STATE.  Synchronous. */
+cs_status cs_debug_set_pair_value(cs_fwd_state *state, int64_t index, uint32_t value);
+
+/* Measured issue rates of the two arithmetic pipes the blend kernels load, on `device`:
+   out[0] = ex2.approx results per clock per SM (the transcendental unit), out[1] = FP32 fused
+   multiply-adds per clock per SM, out[2] = the SM clock during the measurement (MHz), out[3] =
+   the number of SMs.  Each is the median over SMs of results over the cycles (clock64) the SM
+   spent on a launch of 8 independent dependency chains per thread; about a millisecond of GPU
+   time, synchronous, two small cudaMalloc'd buffers.  Errors: CS_ERR_ARG, CS_ERR_CUDA. */
+cs_status cs_measure_alu_rates(int32_t device, double *out);
 
 /* Work actually done by the two blend kernels of a forward state, counted by instrumented
    variants of the kernels (the state's pair lists are re-blended; outputs are unchanged).

@@ -6,6 +6,7 @@ projected (Eq. 4), their 2D hull becomes lines, delta/sigma are scaled by the ca
 in the CUDA library behind include/convex_splat.h; this package only marshals arguments.
 """
 from .rasterizer import (ARRAYS, PARAMS, WORK_FIELDS, Context, RefineSettings, SceneTensors, Server,  # noqa: F401
+                         alu_rates,
                          Settings, State, TrainConfig, Trainer, adam_step, backward, camera_struct, forward,
                          launch_count, loss_l1_dssim, profile_enable, profile_read, refine, render, step_host,
                          work_counts)

@@ -72,6 +72,8 @@ _PROTOTYPES = {
     "cs_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "cs_kernel_launch_count": (ctypes.c_uint64, []),
     "cs_work_counts": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "cs_measure_alu_rates": (ctypes.c_int, [ctypes.c_int32, _P]),
+    "cs_debug_set_pair_value": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint32]),
     "cs_forward_static": (ctypes.c_int, [ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera),
                                          ctypes.POINTER(CsSettings), _P, _P, _P]),
     "cs_loss_l1_dssim": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,

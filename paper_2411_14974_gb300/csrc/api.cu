@@ -187,7 +187,30 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
 cudaError_t cs::pool_alloc(cs_context *ctx, void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
-    return cudaMallocFromPoolAsync(p, (bytes + 255) & ~(size_t)255, ctx->pool, s);
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
+#if CS_CHECKED
+    // checked builds hand out every buffer filled with 0xff bytes (NaN as float): a read of a
+    // buffer before it is written then shows in the results
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0xff, bytes, s);
+#endif
+    return e;
+}
+
+cs_status cs::take_device_status(cudaStream_t s, const char *what) {
+#if CS_CHECKED
+    unsigned bits = 0;
+    cudaError_t e = take_status_blend(&bits, s);
+    if (e == cudaSuccess) e = take_status_sort(&bits, s);
+    if (e != cudaSuccess) return fail_cuda(e, what);
+    if (bits)
+        return fail(CS_ERR_DEVICE, "%s: device status 0x%x (1 tile range, 2 record index, 4 hull count, 8 pair slot, "
+                    "16 tile index, 32 sort slot outside its buffer; the accesses were skipped)", what, bits);
+#else
+    (void)s;
+    (void)what;
+#endif
+    return CS_OK;
 }
 
 void cs::pool_free(void *p, cudaStream_t s) {
@@ -450,7 +473,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
         CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii, s->bboxes,
-                                 R, local_bits, s->mask_shift, s->pair_keys, s->pair_vals, stream),
+                                 R, local_bits, s->mask_shift, s->pair_keys, s->pair_vals, stream, (uint32_t)P),
                "emit pairs");
         pool_free(radii, stream);
         radii = nullptr;
@@ -473,14 +496,27 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             t = s->pair_vals; s->pair_vals = pv_b; pv_b = t;
         }
         CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->views_dev, local_bits, s->mask_shift, s->ranges, tiles,
-                                  stream),
+                                  stream, V),
                "tile ranges");
     }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);
         BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles, s->k,
                     s->pair_keys, s->mask_shift};
-        CS_TRY(launch_blend_forward(a, stream), "blend");
+        a.n_pairs = (uint32_t)P;
+        a.n_records = (uint32_t)R;
+        if (s->view_done.size() == (size_t)V) {
+            for (int v = 0; v < V; ++v) {  // one launch per view, each view's completion recorded
+                const ViewDesc &vd = s->views[v];
+                BlendArgs av = a;
+                av.tile_offset = vd.tile_base;
+                av.n_tiles = (uint32_t)(vd.tiles_x * vd.tiles_y);
+                CS_TRY(launch_blend_forward(av, stream), "blend");
+                CS_TRY(cudaEventRecord(s->view_done[v], stream), "record view");
+            }
+        } else {
+            CS_TRY(launch_blend_forward(a, stream), "blend");
+        }
     }
     for (int v = 0; v < V; ++v) {
         const ViewDesc &vd = s->views[v];
@@ -541,12 +577,30 @@ extern "C" cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs
         vd.t_final = t_final ? t_final + (size_t)v * hw : nullptr;
     }
     st = run_forward(ctx, s, stream);
+    if (st == CS_OK) st = take_device_status(stream, "cs_forward");
     if (st != CS_OK || !state_out) {
         state_free(s);
         return st;
     }
     *state_out = s;
     return CS_OK;
+}
+
+extern "C" cs_status cs_debug_set_pair_value(cs_fwd_state *s, int64_t index, uint32_t value) {
+    if (!s) return fail(CS_ERR_ARG, "state is NULL");
+#if CS_CHECKED
+    if (index < 0 || index >= s->n_pairs) return fail(CS_ERR_ARG, "pair %lld outside 0..%lld", (long long)index,
+                                                      (long long)s->n_pairs);
+    DeviceGuard dg(s->ctx->device);
+    cudaError_t e = cudaMemcpyAsync(s->pair_vals + index, &value, sizeof value, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "cs_debug_set_pair_value");
+    return CS_OK;
+#else
+    (void)index;
+    (void)value;
+    return fail(CS_ERR_STATE, "cs_debug_set_pair_value: only in checked builds");
+#endif
 }
 
 extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
@@ -570,6 +624,8 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
             StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
             BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k,
                         s->pair_keys, s->mask_shift};
+            a.n_pairs = (uint32_t)s->n_pairs;
+            a.n_records = (uint32_t)s->n_records;
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }
@@ -582,6 +638,7 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         if (e != cudaSuccess) st_code = fail_cuda(e, "backward");
     }
     pool_free(grads, stream);
+    if (st_code == CS_OK) st_code = take_device_status(stream, "cs_backward");
     return st_code;
 }
 
@@ -709,6 +766,8 @@ extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, cons
     const int V = (int)s->views.size();
     BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k,
                         s->pair_keys, s->mask_shift};
+    a.n_pairs = (uint32_t)s->n_pairs;
+    a.n_records = (uint32_t)s->n_records;
     if (e == cudaSuccess) e = launch_blend_forward(a, stream, dc);
     if (e == cudaSuccess && dL_dimage && s->n_records) {
         e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);

@@ -4,10 +4,13 @@
 // pixel; backward: 128 threads per tile, each warp an 8x8 block, each thread two pixels (rows r
 // and r + 4).  The warps work independently (no CTA barrier).  A warp walks the tile's
 // depth-ordered pairs, keeping those whose record's pixel box reaches its block (the block-mask
-// bit carried in the pair key, or the box itself), 32 at a time: each lane stages one record in
-// the warp's shared-memory slice, re-expressed relative to the warp's block origin so that every
-// line is two FMAs per pixel, and tests whether any pixel of the block can pass the line
-// pre-test; the warp then evaluates only the records of the resulting ballot.  Per pixel and
+// bit carried in the pair key, or the box itself), 32 at a time, and stages their records in its
+// shared-memory slice (the forward copies the 32 records with coalesced cp.async, four whole
+// records per instruction, and each lane then rewrites its own in place; the backward's lanes
+// load theirs with vector loads): each record is re-expressed relative to the warp's block
+// origin so that every line is two FMAs per pixel, and tested for whether any pixel of the block
+// can pass the line pre-test; the warp then evaluates only the records of the resulting ballot.
+// Per pixel and
 // convex (Eq. S1, S2 and 5):
 //     s_t  = log2(e) d delta L_t(q)                     (T lines, 2 FMA each)
 //     phi2 = max_t s_t + log2 sum_t 2^(s_t - max)       (= log2(e) phi)
@@ -18,25 +21,77 @@
 // its transmittance below t_min.
 //
 // The backward walks each tile's list in reverse from the last contributor of each pixel,
-// recovering T before a pair as T_after / (1 - alpha), and accumulates d(loss)/d(record) per
-// convex: the 3K + 5 per-pixel terms are summed across the warp by a reduce-scatter (16 + 8
-// words, 25 shuffles at K = 6, lane l ends with word l) and added to the convex's gradient record
-// by one coalesced atomic instruction per (warp, record).
+// recovering T before a pair as T_after / (1 - alpha) and carrying, per pixel, the colour seen
+// behind the pair only through its product with dL/dC (the one scalar dL/dalpha needs), and
+// accumulates d(loss)/d(record) per convex: the 3K + 5 per-pixel terms are summed across the warp
+// by a reduce-scatter (16 + 8 words, 25 shuffles at K = 6, lane l ends with word l) and added to
+// the convex's gradient record by one coalesced atomic instruction per (warp, record).
 #include "cs_common.cuh"
 
 namespace cs {
 namespace {
 
+#if CS_CHECKED
+__device__ unsigned int g_status_blend;  // bits of the failed index tests of the blend kernels
+__device__ __forceinline__ bool checked(bool ok, unsigned bit) {
+    if (!ok) atomicOr(&g_status_blend, bit);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool checked(bool ok, unsigned) { return true; }
+#endif
+
 constexpr int FWD_THREADS = 256;  // forward: 8 warps per tile, a warp an 8x4 block, a lane one pixel
 constexpr int BWD_THREADS = 128;  // backward: 4 warps per tile, a warp an 8x8 block, a lane rows r, r + 4
-constexpr int SREC = 11;          // float4 per staged record
-// staged record (one per lane of a warp):
+// staged record (one per lane of a warp), SREC<K> float4:
 //   [0] = (sigma', pre-test bound, o, T)   [1] = (r, g, b, record index)
 //   [2] = (block origin minus anchor vertex: x, y, -, -)
 //   [3 + t] = (A_t, B_t, C_t relative to the upper 8x4 block origin, C_t relative to the lower one)
 // The forward's 8x4 blocks and the backward's two 8x4 halves of an 8x8 block are re-based to the
 // same origins, so both kernels evaluate every pair with identical binary32 values.
+template <int K>
+constexpr int SREC = 3 + K;
+// 16-byte chunks of a screen record that hold its header and K lines
+template <int K>
+constexpr int REC_CHUNKS = (R_LINES + 3 * K + 3) / 4;
+// a warp's staging buffer, in float4: the 32 raw records (128 B each) land there first, then each
+// lane re-writes its own record in the staged form over them
+template <int K>
+constexpr int STAGE_F4 = 32 * (SREC<K> > REC_WORDS / 4 ? SREC<K> : REC_WORDS / 4);
 constexpr float LN2 = 0.6931471805599453f;
+
+__device__ __forceinline__ void cp_async_cg16(void *dst, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+
+// Copies the screen records of the nh gathered pairs (slots sidx[0..nh)) into the warp's staging
+// buffer with coalesced 16-byte cp.async: one instruction moves four whole records, eight lanes
+// per record, chunk c of the record in slot s landing at float4 8 s + (c ^ (s & 7)) (the XOR
+// spreads the 32 records' chunk c over all banks for the per-lane reads that follow).  Returns
+// this lane's record index (lane < nh).  The copies are complete and visible to the whole warp
+// on return.
+template <int K>
+__device__ __forceinline__ uint32_t copy_records(float4 *buf, const float4 *__restrict__ records,
+                                                 const uint32_t *__restrict__ pair_vals, const uint32_t *sidx, int nh,
+                                                 int lane, uint32_t n_records) {
+    uint32_t r = lane < nh ? __ldg(pair_vals + sidx[lane]) : 0u;
+    if (!checked(r < n_records, CS_BAD_RECORD)) r = 0;
+    const int c = lane & 7;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int slot = 4 * k + (lane >> 3);
+        const uint32_t rs = __shfl_sync(0xffffffffu, r, slot);
+        if (slot < nh && c < REC_CHUNKS<K>)
+            cp_async_cg16(buf + 8 * slot + (c ^ (slot & 7)), records + (size_t)rs * (REC_WORDS / 4) + c);
+    }
+    cp_async_commit_wait();
+    __syncwarp();
+    return r;
+}
 
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -54,17 +109,82 @@ __device__ __forceinline__ float rcp(float x) {
     return y;
 }
 
-// Stage record r for the pixel block of 8 x ROWS pixels whose first pixel centre is
-// (ox + 0.5, oy + 0.5) in image coordinates (ROWS = 4: one 8x4 block; ROWS = 8: two stacked 8x4
-// blocks with origins oy and oy + 4).  Returns false when no pixel of the block can pass the
-// line pre-test: for some line, its smallest value over the block's pixel centres exceeds the
-// bound (with a margin for the per-pixel rounding).
+// Stage record r, whose raw copy sits in the staging buffer at slot `lane` (see copy_records), for
+// the pixel block of 8 x ROWS pixels whose first pixel centre is (ox + 0.5, oy + 0.5) in image
+// coordinates (ROWS = 4: one 8x4 block; ROWS = 8: two stacked 8x4 blocks with origins oy and
+// oy + 4), writing the staged form into the same buffer at slot `lane`.  Every lane of the warp
+// calls it (lanes at or beyond nh stage nothing).  Returns false when no pixel of the block can
+// pass the line pre-test: for some line, its smallest value over the block's pixel centres exceeds
+// the bound (with a margin for the per-pixel rounding).
 template <int ROWS, int K>
-__device__ __forceinline__ bool stage_record(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
+__device__ __forceinline__ bool stage_record(float4 *buf, int lane, int nh, uint32_t r, float ox, float oy,
+                                             const Settings &st) {
+    // the raw record of this lane, read in full before any lane overwrites the buffer
+    const float4 *raw = buf + 8 * lane;
+    const int sw = lane & 7;
+    float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
+    float L[3 * K + 3];
+    if (lane < nh) {
+        h0 = raw[0 ^ sw];
+        h1 = raw[1 ^ sw];
+#pragma unroll
+        for (int q = 0; q < REC_CHUNKS<K> - 2; ++q) {
+            const float4 v = raw[(q + 2) ^ sw];
+            L[4 * q] = v.x; L[4 * q + 1] = v.y; L[4 * q + 2] = v.z; L[4 * q + 3] = v.w;
+        }
+    }
+    __syncwarp();
+    if (lane >= nh) return false;
+    float4 *dst = buf + SREC<K> * lane;
+    int T = (int)hull_pack_count(__float_as_uint(h1.w));
+    if (!checked(T >= 3 && T <= K, CS_BAD_HULL)) T = 0;
+    const float offx = ox - h0.x, offy = oy - h0.y, offy2 = (oy + 4.0f) - h0.y;
+    // pre-test: alpha < tau whenever sigma' max_t s_t > log2(o/tau - 1) (phi2 >= max_t s_t); the
+    // bound is widened so that it never rejects a pair the full evaluation keeps
+    float bound = __int_as_float(0x7f800000);
+    if (st.tau > 0.f) {
+        const float x = h0.w / st.tau - 1.0f;
+        if (isfinite(x)) {
+            const float b = lg2(x) * rcp(h0.z);
+            bound = b + fabsf(b) * 0x1p-10f + 0x1p-10f;
+        }
+    }
+    bool pass = true;
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        if (t < T) {
+            const float A = L[3 * t], B = L[3 * t + 1], C = L[3 * t + 2];
+            const float Cp = fmaf(A, offx, fmaf(B, offy, C));
+            const float Cp2 = ROWS == 8 ? fmaf(A, offx, fmaf(B, offy2, C)) : 0.f;
+            dst[3 + t] = make_float4(A, B, Cp, Cp2);
+            const float margin = (fabsf(Cp) + 8.f * (fabsf(A) + fabsf(B))) * 0x1p-20f + 0x1p-20f;
+            const float mn = Cp + fminf(0.5f * A, 7.5f * A) + fminf(0.5f * B, ((float)ROWS - 0.5f) * B);
+            pass = pass && !(mn > bound + margin);
+        } else {
+            // an unused slot: a line that is -inf everywhere adds 2^-inf = 0 to the sum and never
+            // wins the maximum, so every record is evaluated with K lines
+            const float ninf = -__int_as_float(0x7f800000);
+            dst[3 + t] = make_float4(0.f, 0.f, ninf, ninf);
+        }
+    }
+    dst[0] = make_float4(h0.z, bound, h0.w, __int_as_float(T));
+    dst[1] = make_float4(h1.x, h1.y, h1.z, __uint_as_float(r));
+    dst[2] = make_float4(offx, offy, 0.f, 0.f);
+    return pass;
+}
+
+// The backward's staging: each lane loads its own record r from global memory with 16-byte
+// vector loads (as many as the record's hull lines need) and writes the staged form to dst, for
+// the same pixel blocks and with the same values as stage_record.  (Staging through the warp's
+// cp.async copies, as the forward does, costs this kernel register spills at its occupancy of
+// 7 CTAs per SM and was measured slower.)  Returns the same pre-test result.
+template <int ROWS, int K>
+__device__ __forceinline__ bool stage_record_ldg(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
                                              float oy, const Settings &st) {
     const float4 *src = records + (size_t)r * (REC_WORDS / 4);
     const float4 h0 = __ldg(src), h1 = __ldg(src + 1);
-    const int T = (int)hull_pack_count(__float_as_uint(h1.w));
+    int T = (int)hull_pack_count(__float_as_uint(h1.w));
+    if (!checked(T >= 3 && T <= K, CS_BAD_HULL)) T = 0;
     float L[3 * KMAX];
 #pragma unroll
     for (int q = 0; q < (3 * K + 3) / 4; ++q) {
@@ -202,8 +322,11 @@ __device__ __forceinline__ int gather_candidates(const BlendArgs &a, float x0, f
             if (a.mask_shift) {  // the pair key carries the box test of every 8x4 block of the tile
                 hit = ((__ldg(a.pair_keys + i) >> a.mask_shift) & block_bits) != 0u;
             } else {
-                const float4 bb = __ldg(a.bboxes + a.pair_vals[i]);
-                hit = !(bb.z < x0 || bb.x > x1 || bb.w < y0 || bb.y > y1);
+                const uint32_t r = a.pair_vals[i];
+                if (checked(r < a.n_records, CS_BAD_RECORD)) {
+                    const float4 bb = __ldg(a.bboxes + r);
+                    hit = !(bb.z < x0 || bb.x > x1 || bb.w < y0 || bb.y > y1);
+                }
             }
         }
         const uint32_t hits = __ballot_sync(0xffffffffu, hit);
@@ -235,9 +358,9 @@ __device__ __forceinline__ void tile_of(const ViewDesc &vd, uint32_t g, int &tx,
 
 template <bool COUNT, int K>
 __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, unsigned long long *counts) {
-    __shared__ float4 srec[FWD_THREADS / 32][32 * SREC];
+    __shared__ float4 srec[FWD_THREADS / 32][STAGE_F4<K>];
     __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
-    const uint32_t g = blockIdx.x;
+    const uint32_t g = a.tile_offset + blockIdx.x;
     const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
     int tx, ty;
     tile_of(vd, g, tx, ty);
@@ -247,7 +370,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
     const bool inside = px < vd.width && py < vd.height;
     const float ox = (float)bx, oy = (float)by;
     const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;
-    const uint2 range = a.ranges[g];
+    uint2 range = a.ranges[g];
+    if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
     const Settings st = a.st;
     float4 *wrec = srec[w];
     uint32_t *sidx = sidx_all[w];
@@ -262,8 +386,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
         // this warp's 8x4 block is column w & 1, row w >> 1 of the tile: mask bit w
         const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, 1u << w, range.x, range.y,
                                                 pos, sidx, lane);
-        bool pass = false;
-        if (lane < nh) pass = stage_record<4, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
+        const uint32_t rl = copy_records<K>(wrec, a.records, a.pair_vals, sidx, nh, lane, a.n_records);
+        const bool pass = stage_record<4, K>(wrec, lane, nh, rl, ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         if (!done) {
@@ -275,7 +399,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
                 const uint32_t j2 = bits ? (uint32_t)(__ffs(bits) - 1) : j1;
                 const bool two = bits != 0;
                 bits &= bits - 1;
-                const float4 *rec1 = wrec + j1 * SREC, *rec2 = wrec + j2 * SREC;
+                const float4 *rec1 = wrec + j1 * SREC<K>, *rec2 = wrec + j2 * SREC<K>;
                 PairTerms p1, p2;
                 const int code1 = eval_pair<0, K>(rec1, lx, ly, st, p1);
                 const int code2 = two ? eval_pair<0, K>(rec2, lx, ly, st, p2) : 0;
@@ -328,7 +452,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
 struct BwdPixels {
     float Tc[2];               // transmittance behind the pair being undone
     float G0[2], G1[2], G2[2];  // dL/dC
-    float S0[2], S1[2], S2[2];  // colour seen behind the current pair, times T
+    float GS[2];               // dL/dC . (colour seen behind the current pair, times T)
     uint32_t last[2];          // pairs at or beyond this index did not contribute
 };
 
@@ -404,15 +528,14 @@ __device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint3
         const float om = 1.0f - p.alpha;
         const float inv = rcp(om);  // om >= 1 - alpha_max > 0
         const float Tn = q.Tc[k] * inv;  // transmittance in front of this pair
-        const float dalpha = q.G0[k] * (Tn * c.x - q.S0[k] * inv) + q.G1[k] * (Tn * c.y - q.S1[k] * inv) +
-                             q.G2[k] * (Tn * c.z - q.S2[k] * inv);
+        // dC/dalpha = T_n c - S / (1 - alpha), S the colour behind: only dL/dC . S is needed
+        const float Gc = fmaf(q.G2[k], c.z, fmaf(q.G1[k], c.y, q.G0[k] * c.x));
+        const float dalpha = fmaf(Tn, Gc, -q.GS[k] * inv);
         const float ta = Tn * p.alpha;
         v[PW::RGB] += q.G0[k] * ta;
         v[PW::RGB + 1] += q.G1[k] * ta;
         v[PW::RGB + 2] += q.G2[k] * ta;
-        q.S0[k] = fmaf(ta, c.x, q.S0[k]);
-        q.S1[k] = fmaf(ta, c.y, q.S1[k]);
-        q.S2[k] = fmaf(ta, c.z, q.S2[k]);
+        q.GS[k] = fmaf(ta, Gc, q.GS[k]);
         q.Tc[k] = Tn;
         if (p.oI < st.alpha_max) {
             v[PW::OPA] += dalpha * p.I;
@@ -478,9 +601,9 @@ template <bool COUNT, int K>
 __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
-    __shared__ float4 srec[BWD_THREADS / 32][32 * SREC];
+    __shared__ float4 srec[BWD_THREADS / 32][STAGE_F4<K>];
     __shared__ uint32_t sidx_all[BWD_THREADS / 32][32];
-    const uint32_t g = blockIdx.x;
+    const uint32_t g = a.tile_offset + blockIdx.x;
     const int v = find_view(a.views, a.n_views, g);
     const ViewDesc &vd = a.views[v];
     int tx, ty;
@@ -491,7 +614,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
     const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;  // within each 8x4 half
     const int px = bx + (lane & 7);
     const Settings st = a.st;
-    const uint2 range = a.ranges[g];
+    uint2 range = a.ranges[g];
+    if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
     float4 *wrec = srec[w];
     uint32_t *sidx = sidx_all[w];
 
@@ -516,10 +640,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
             q.last[k] = vd.n_last[pix];
             cnt[5]++;
         }
-        // colour seen behind the current pair: T_after * (its colour) summed from the back
-        q.S0[k] = q.Tc[k] * st.bg[0];
-        q.S1[k] = q.Tc[k] * st.bg[1];
-        q.S2[k] = q.Tc[k] * st.bg[2];
+        // colour seen behind the current pair (T_after times its colour, summed from the back),
+        // kept as its product with dL/dC; it starts with the background
+        q.GS[k] = q.Tc[k] * fmaf(q.G2[k], st.bg[2], fmaf(q.G1[k], st.bg[1], q.G0[k] * st.bg[0]));
         lmax = max(lmax, q.last[k]);
     }
     const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
@@ -530,13 +653,17 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
         const int nh = gather_candidates<true>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 7.5f, bbits, range.x, range.y,
                                                pos, sidx, lane);
         bool pass = false;
-        if (lane < nh) pass = stage_record<8, K>(wrec + lane * SREC, a.records, a.pair_vals[sidx[lane]], ox, oy, st);
+        if (lane < nh) {
+            uint32_t r = a.pair_vals[sidx[lane]];
+            if (!checked(r < a.n_records, CS_BAD_RECORD)) r = 0;
+            pass = stage_record_ldg<8, K>(wrec + lane * SREC<K>, a.records, r, ox, oy, st);
+        }
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
         while (bits) {  // warp-uniform; slots hold decreasing pair indices
             const int j = __ffs(bits) - 1;
             bits &= bits - 1;
-            const float4 *rec = wrec + j * SREC;
+            const float4 *rec = wrec + j * SREC<K>;
             const uint32_t idx = sidx[j];
             using PW = PackedWords<K>;
             float v[PW::N];
@@ -591,6 +718,22 @@ static void blend_backward_k(const BlendArgs &a, const float *dL_dimage, int64_t
         k_blend_backward<true, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
     else
         k_blend_backward<false, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
+}
+
+cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
+#if CS_CHECKED
+    unsigned v = 0;
+    const unsigned zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_blend, sizeof v, 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_status_blend, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) *bits |= v;
+    return e;
+#else
+    (void)bits;
+    (void)s;
+    return cudaSuccess;
+#endif
 }
 
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,

@@ -48,6 +48,9 @@ struct cs_fwd_state {
     uint32_t *n_last = nullptr;
     float *t_final_own = nullptr;          // [pixels of all views], read by the backward
     std::vector<float *> user_t_final;     // caller's T_final buffers (copied to after the blend)
+    // when not empty (one event per view): the forward blends view by view, in view order, and
+    // records view_done[v] on the stream once view v's image is written
+    std::vector<cudaEvent_t> view_done;
 };
 
 namespace cs {
@@ -61,6 +64,9 @@ cs_status check_scene(const cs_scene *s);
 void fill_view(ViewDesc &vd, const cs_camera &c);
 Settings to_settings(const cs_settings &s);
 cs_status run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream);
+// checked builds: after the work enqueued on s, the kernels' failed index tests as CS_ERR_DEVICE
+// (synchronises s); production builds: CS_OK without synchronising
+cs_status take_device_status(cudaStream_t s, const char *what);
 void state_free(cs_fwd_state *s);
 
 // makes ctx's device current for the lifetime of the guard

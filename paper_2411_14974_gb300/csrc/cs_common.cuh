@@ -126,9 +126,32 @@ cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
                               const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
                               int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
-                              cudaStream_t s);
+                              cudaStream_t s, uint32_t n_pairs = 0xffffffffu);
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
-                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s);
+                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s, int n_views);
+
+// ---- checked builds ---------------------------------------------------------------------------
+// Built with -DCS_CHECKED=1, the kernels test every index that an inconsistent upstream value could
+// send out of bounds before using it; a failed test skips (or clamps) the access and sets a bit in
+// its translation unit's device status word, and the entry points read and clear those words once
+// their stream has finished, returning CS_ERR_DEVICE.  Transient buffers are also filled with 0xff
+// bytes (NaN as float) when they are taken from the pool, so that reading a buffer before it is
+// written changes the results.  Production builds compile all of it out.
+#ifndef CS_CHECKED
+#define CS_CHECKED 0
+#endif
+enum : uint32_t {
+    CS_BAD_RANGE = 1u,      // a tile's pair range outside the pair list
+    CS_BAD_RECORD = 2u,     // a pair's record index beyond the records
+    CS_BAD_HULL = 4u,       // a record's hull line count outside 3..K
+    CS_BAD_PAIR_SLOT = 8u,  // an emitted pair beyond the pair list
+    CS_BAD_TILE = 16u,      // a tile index beyond the tiles
+    CS_BAD_SORT_SLOT = 32u  // a radix-sort destination beyond the items
+};
+// OR into *bits, and clear, the status words of the blend kernels / of the sort, emission and
+// range kernels, after the work enqueued on s so far (synchronises s; no-ops in production builds)
+cudaError_t take_status_blend(unsigned *bits, cudaStream_t s);
+cudaError_t take_status_sort(unsigned *bits, cudaStream_t s);
 
 struct BlendArgs {
     const ViewDesc *views;
@@ -142,6 +165,9 @@ struct BlendArgs {
     int k;  // points per convex: at most k hull lines per record
     const uint32_t *pair_keys;  // with block masks when mask_shift > 0
     int mask_shift;             // 0: no masks, the gather tests the records' pixel boxes
+    uint32_t tile_offset = 0;   // global index of the launch's first tile (its tiles: n_tiles from there)
+    uint32_t n_pairs = 0xffffffffu;    // pair-list length and record count: bounds of the checked
+    uint32_t n_records = 0xffffffffu;  // builds' index tests (all ones: unknown)
 };
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);

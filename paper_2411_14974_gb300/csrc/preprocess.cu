@@ -17,9 +17,11 @@ namespace {
 template <int K, int STG>
 __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *__restrict__ views, Settings st,
                                                             PreprocessOut out) {
-    const ViewDesc &vd = views[blockIdx.y];
+    // view fastest in the launch order: the blocks of every view over the same convexes run side by
+    // side, so a batch of views of one scene reads the scene from HBM about once (L2 serves the rest)
+    const ViewDesc &vd = views[blockIdx.x];
     const int64_t n = vd.n;
-    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
+    const int64_t i0 = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * PRE_THREADS;
     if (i0 >= n) return;  // whole block
     constexpr int PS = (3 * K) | 1;  // odd stride of a convex's staged points: no bank conflicts
     __shared__ float sp[PRE_THREADS * PS];
@@ -330,8 +332,8 @@ static void launch_pre_k(dim3 grid, cudaStream_t s, int storage, const ViewDesc 
 cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n, int k,
                               const Settings &st, const PreprocessOut &out, cudaStream_t s) {
     if (max_n <= 0 || n_views <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((max_n + PRE_THREADS - 1) / PRE_THREADS), (unsigned)n_views);
-    const int storage = views_host[0].storage;  // one scene per launch
+    const dim3 grid = view_major_grid(n_views, max_n);
+    const int storage = views_host[0].storage;  // one storage type per launch
     switch (k) {
         case 3: launch_pre_k<3>(grid, s, storage, views_dev, st, out); break;
         case 4: launch_pre_k<4>(grid, s, storage, views_dev, st, out); break;

@@ -30,8 +30,9 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
     __shared__ float s_dp[ATOMIC ? 1 : PRE_THREADS * PS];
     __shared__ __align__(16) float ssh[PRE_THREADS * (STG == CS_STORE_F32 ? SH_STAGE_WORDS : SH_STAGE_WORDS / 2 + 2)];
     __shared__ float s_dsh[SEP_DSH ? PRE_THREADS * SS : 1];
-    const ViewDesc &vd = views[blockIdx.y];
-    const int64_t i0 = (int64_t)blockIdx.x * PRE_THREADS;
+    // view fastest in the launch order (see k_preprocess)
+    const ViewDesc &vd = views[blockIdx.x];
+    const int64_t i0 = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * PRE_THREADS;
     if (i0 >= vd.n) return;
     const int cnt = (int)min((int64_t)PRE_THREADS, vd.n - i0);
     const int sh_stride = stage_sh<STG>(ssh, vd.sh, i0, cnt, SW);
@@ -342,7 +343,7 @@ cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, i
                                        cudaStream_t s) {
     if (max_n <= 0 || n_views <= 0) return cudaSuccess;
     if (sh_degree < 0 || sh_degree > 3) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((max_n + PRE_THREADS - 1) / PRE_THREADS), (unsigned)n_views);
+    const dim3 grid = view_major_grid(n_views, max_n);
     switch (k) {
         case 3:
             launch_pre_bwd_ks<3>(grid, s, storage, sh_degree, atomic, views_dev, st, records, counts, grad_records, g);

@@ -17,6 +17,15 @@ constexpr int PRE_THREADS = 128;
 constexpr float COORD_LIMIT = 1048576.0f;  // 2^20 px
 constexpr float LOG2E = 1.4426950408889634f;
 
+// Launch grid of the per-(view, convex) kernels: x = view (fastest), y and z = block of
+// PRE_THREADS convexes (y below 65535, z counting the rows of y), so that the blocks of all views
+// over the same convexes are scheduled together.
+inline dim3 view_major_grid(int n_views, int64_t max_n) {
+    const int64_t nblk = (max_n + PRE_THREADS - 1) / PRE_THREADS;
+    const int64_t y = nblk < 65535 ? nblk : 65535;
+    return dim3((unsigned)n_views, (unsigned)y, (unsigned)((nblk + y - 1) / y));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Exact orientation sign of three binary32 points: sign((b-a) x (c-a)).
 // A binary32 evaluation with a forward error bound decides almost every case; the rest are

@@ -4,12 +4,15 @@
 //   caller threads   cs_server_submit queues a request (scene, camera, output buffer);
 //   worker           admits queued requests in arrival order into a batch (at most max_batch
 //                    views, same K, estimated transient memory within the budget left by the
-//                    batches still on the GPU), runs the batched forward (one binning and sort for
-//                    all views, one blend launch over every (view, tile)) on one of two streams,
-//                    records a completion event and goes back for the next batch -- so the
-//                    preprocess and sorts of batch k+1 overlap the blend of batch k;
-//   finisher         waits for the batches in order, frees their buffers, returns their memory
-//                    to the budget and posts one completion per request.
+//                    batches still on the GPU), orders the batch's views by estimated cost
+//                    (smallest first), runs the batched forward (one preprocess, binning and sort
+//                    for all views, then one blend launch per view, each followed by that view's
+//                    completion event) on one of two streams and goes back for the next batch --
+//                    so the preprocess and sorts of batch k+1 overlap the blends of batch k;
+//   finisher         waits for the batches in order and, within a batch, for each view's event,
+//                    posting each request's completion as soon as its own image is written; then
+//                    frees the batch's buffers and returns its memory to the budget.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -39,12 +42,13 @@ struct Request {
 struct Scene {
     cs_scene sc;
     bool alive = true;
-    double pairs_per_convex = 4.0;  // tile pairs per convex at 1920x1080, learnt from past batches
+    double pairs_per_convex = 8.0;  // tile pairs per convex at 1920x1080, learnt from past batches
     int64_t busy = 0;               // views of this scene in admitted batches
 };
 
 struct Batch {
     std::vector<Request> reqs;
+    std::vector<cudaEvent_t> view_done;  // one per request, recorded after its view's blend
     cs_fwd_state *state = nullptr;
     cudaEvent_t done = nullptr;
     size_t est = 0;
@@ -84,9 +88,17 @@ struct cs_server {
         const double px = (double)c.width * c.height;
         const double pairs = s.pairs_per_convex * (double)s.sc.n * (px / (1920.0 * 1080.0)) + 64.0;
         const double tiles = (double)((c.width + 15) / 16) * ((c.height + 15) / 16);
-        // records, keys, counts, rects, tile-test radii, sort temporaries; pairs and their sort buffers; per pixel
-        // T_final and last contributor; tile ranges
-        return (size_t)((double)s.sc.n * 180.0 + pairs * 16.0 + px * 8.0 + tiles * 8.0 + 4096.0);
+        // records, keys, counts, rects, pixel boxes, tile-test radii, depth-sort buffers and offsets
+        // (about 185 bytes per convex); pairs and their sort buffers; per pixel T_final and last
+        // contributor; tile ranges
+        return (size_t)((double)s.sc.n * 192.0 + pairs * 16.0 + px * 8.0 + tiles * 8.0 + 4096.0);
+    }
+
+    // bytes the pool has handed out and not yet taken back (the batches' real allocations)
+    size_t pool_used() const {
+        uint64_t used = 0;
+        if (cudaMemPoolGetAttribute(ctx->pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) return 0;
+        return (size_t)used;
     }
 
     void complete_locked(const Request &r, cs_status st, int batch, Clock::time_point now) {
@@ -119,6 +131,13 @@ void cs_server::run_worker() {
         int K = -1;
         size_t est = 0;
         const Clock::time_point now = Clock::now();
+        // memory taken by the batches on the GPU: their estimates, or what the pool really holds
+        // for them when that is more (nothing is held once none is in flight)
+        size_t held = inflight_bytes;
+        if (!inflight.empty()) {
+            const size_t used = pool_used();
+            if (used > held) held = used;
+        }
         for (auto it = pending.begin(); it != pending.end() && (int)b->reqs.size() < max_batch;) {
             auto sit = scenes.find(it->scene);
             if (sit == scenes.end() || !sit->second.alive) {
@@ -137,7 +156,7 @@ void cs_server::run_worker() {
                 it = pending.erase(it);
                 continue;
             }
-            if (inflight_bytes + est + e > budget) break;  // wait until batches on the GPU free memory
+            if (held + est + e > budget) break;  // wait until batches on the GPU free memory
             K = sc.sc.k;
             est += e;
             it->t_admit = now;
@@ -150,6 +169,9 @@ void cs_server::run_worker() {
             if (!inflight.empty()) cv_mem.wait(lk);  // memory frees up when a batch finishes
             continue;
         }
+        // cheapest views first: their images are written, and their requests completed, first
+        std::stable_sort(b->reqs.begin(), b->reqs.end(),
+                         [](const Request &x, const Request &y) { return x.est < y.est; });
         b->est = est;
         inflight_bytes += est;
         if (inflight_bytes > peak_bytes) peak_bytes = inflight_bytes;
@@ -179,6 +201,14 @@ void cs_server::run_worker() {
 
         cudaStream_t stream = streams[next_stream];
         next_stream ^= 1;
+        if (s) {
+            b->view_done.assign(b->reqs.size(), nullptr);
+            for (cudaEvent_t &e : b->view_done)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
+            bool all = true;
+            for (cudaEvent_t e : b->view_done) all = all && e;
+            if (all) s->view_done = b->view_done;  // else one blend launch, completions at the batch's end
+        }
         if (!s) {
             b->status = fail(CS_ERR_NOMEM, "out of host memory");
         } else {
@@ -211,6 +241,24 @@ void cs_server::run_finisher() {
             b = inflight.front();
         }
         cs_status st = b->status;
+        const bool per_view = b->state && b->state->view_done.size() == b->reqs.size() && st == CS_OK;
+        // each view's request completes once its own blend has run (an event that was never
+        // recorded, after a failed forward, reads as complete)
+        for (size_t v = 0; v < b->view_done.size(); ++v) {
+            cudaEvent_t ev = b->view_done[v];
+            cudaError_t e = cudaSuccess;
+            if (ev && per_view) {
+                while ((e = cudaEventQuery(ev)) == cudaErrorNotReady)
+                    std::this_thread::sleep_for(std::chrono::microseconds(20));
+                if (e == cudaSuccess) {
+                    std::lock_guard<std::mutex> lk(mu);
+                    complete_locked(b->reqs[v], CS_OK, (int)b->reqs.size(), Clock::now());
+                    b->reqs[v].id = 0;  // posted
+                } else if (st == CS_OK) {
+                    st = fail_cuda(e, "server view");
+                }
+            }
+        }
         if (b->done) {
             cudaError_t e;
             while ((e = cudaEventQuery(b->done)) == cudaErrorNotReady)
@@ -218,6 +266,8 @@ void cs_server::run_finisher() {
             if (e != cudaSuccess && st == CS_OK) st = fail_cuda(e, "server batch");
             cudaEventDestroy(b->done);
         }
+        for (cudaEvent_t ev : b->view_done)
+            if (ev) cudaEventDestroy(ev);
         const Clock::time_point now = Clock::now();
         int64_t pairs = b->state ? b->state->n_pairs : 0;
         if (b->state) state_free(b->state);
@@ -230,7 +280,7 @@ void cs_server::run_finisher() {
                 Scene &sc = scenes[r.scene];
                 sc.busy--;
                 if (st == CS_OK && observed > sc.pairs_per_convex) sc.pairs_per_convex = observed;
-                complete_locked(r, st, (int)b->reqs.size(), now);
+                if (r.id) complete_locked(r, st, (int)b->reqs.size(), now);
             }
             cv_mem.notify_all();
             cv_work.notify_all();
@@ -275,6 +325,8 @@ extern "C" cs_status cs_server_create(int32_t device, size_t budget, int32_t max
             return fail_cuda(e, "cudaStreamCreate");
         }
     }
+    uint64_t zero = 0;  // the pool is the server's own: its high-water mark counts from here
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero);
     cudaSetDevice(prev);
     srv->worker = std::thread([srv] { srv->run_worker(); });
     srv->finisher = std::thread([srv] { srv->run_finisher(); });
@@ -394,5 +446,8 @@ extern "C" cs_status cs_server_stats(cs_server *srv, uint64_t *stats) {
     stats[3] = srv->peak_bytes;
     stats[4] = srv->pending.size();
     stats[5] = on_gpu;
+    uint64_t high = 0;
+    if (cudaMemPoolGetAttribute(srv->ctx->pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess) high = 0;
+    stats[6] = high;
     return CS_OK;
 }

@@ -24,6 +24,17 @@
 namespace cs {
 namespace {
 
+#if CS_CHECKED
+__device__ unsigned int g_status_sort;  // bits of the failed index tests of this file's kernels
+__device__ __forceinline__ bool checked(bool ok, unsigned bit) {
+    if (!ok) atomicOr(&g_status_sort, bit);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool checked(bool ok, unsigned) { return true; }
+#endif
+
+
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -290,6 +301,7 @@ __global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(const uint32_t 
         const uint32_t k = skey[i];
         const uint32_t d = (k >> shift) & mask;
         const uint32_t dst = gbase[d] + ((uint32_t)i - lbase[d]);
+        if (!checked((int64_t)dst < n, CS_BAD_SORT_SLOT)) continue;
         keys_out[dst] = k;
         vals_out[dst] = sval[i];
     }
@@ -343,7 +355,8 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
                        const uint2 *__restrict__ rects, const float4 *__restrict__ records,
                        const float *__restrict__ radii, const float4 *__restrict__ bboxes, int64_t n_records,
-                       int local_bits, int mask_shift, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                       int local_bits, int mask_shift, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                       uint32_t n_pairs) {
     // the block mask of tile (tx, ty) for box bb, at its place in the key (0 without masks)
     auto mask_bits = [&](const float4 &bb, uint32_t tx, uint32_t ty) -> uint32_t {
         return mask_shift ? block_mask(bb, tx, ty) << mask_shift : 0u;
@@ -391,7 +404,7 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
             bs.y = __shfl_sync(0xffffffffu, bb.y, s);
             bs.z = __shfl_sync(0xffffffffu, bb.z, s);
             bs.w = __shfl_sync(0xffffffffu, bb.w, s);
-            if (p < we && fs) {
+            if (p < we && fs && checked(p < n_pairs, CS_BAD_PAIR_SLOT)) {
                 const uint32_t k = p - os, wd = (rx >> 16) - (rx & 0xffffu) + 1;
                 const uint32_t ty = (ry & 0xffffu) + k / wd, tx = (rx & 0xffffu) + k % wd;
                 keys[p] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
@@ -412,8 +425,10 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
         for (uint32_t ty = ty0; ty <= ty1; ++ty)
             for (uint32_t tx = tx0; tx <= tx1; ++tx)
                 if (tile_kept(w + R_LINES, T, w[R_AX], w[R_AY], rk, (int)tx, (int)ty)) {
-                    keys[o] = mask_bits(bb, tx, ty) | hi | (ty * tiles_x + tx);
-                    vals[o] = r;
+                    if (checked(o < n_pairs, CS_BAD_PAIR_SLOT)) {
+                        keys[o] = mask_bits(bb, tx, ty) | hi | (ty * tiles_x + tx);
+                        vals[o] = r;
+                    }
                     ++o;
                 }
     }
@@ -448,8 +463,10 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
             const uint32_t ball = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const uint32_t at = os + (uint32_t)__popc(ball & ((1u << lane) - 1u));
-                keys[at] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
-                vals[at] = rs;
+                if (checked(at < n_pairs, CS_BAD_PAIR_SLOT)) {
+                    keys[at] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
+                    vals[at] = rs;
+                }
             }
             os += (uint32_t)__popc(ball);
         }
@@ -458,11 +475,14 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
 
 // [start, end) of every (view, tile) group of the sorted pairs, stored at the global tile index
 __global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, const ViewDesc *__restrict__ views,
-                         int local_bits, uint32_t key_mask, uint2 *__restrict__ ranges) {
+                         int local_bits, uint32_t key_mask, uint2 *__restrict__ ranges, int n_views,
+                         int64_t n_tiles) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t k = keys[i] & key_mask;
+    if (!checked((int64_t)(k >> local_bits) < n_views, CS_BAD_TILE)) return;
     const uint32_t g = views[k >> local_bits].tile_base + (k & ((1u << local_bits) - 1u));
+    if (!checked((int64_t)g < n_tiles, CS_BAD_TILE)) return;
     if (i == 0 || (keys[i - 1] & key_mask) != k) ranges[g].x = (uint32_t)i;
     if (i == n - 1 || (keys[i + 1] & key_mask) != k) ranges[g].y = (uint32_t)(i + 1);
 }
@@ -577,25 +597,41 @@ cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
                               const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
                               int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
-                              cudaStream_t s) {
+                              cudaStream_t s, uint32_t n_pairs) {
     if (n_records <= 0) return cudaSuccess;
     if (mask_shift < 0 || (mask_shift > 0 && mask_shift + BLOCK_MASK_BITS > 32)) return cudaErrorInvalidValue;
     k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
                                                                rects, records, radii, bboxes, n_records, local_bits,
-                                                               mask_shift, pair_keys, pair_vals);
+                                                               mask_shift, pair_keys, pair_vals, n_pairs);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
-                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s) {
+                               int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s, int n_views) {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
     const uint32_t key_mask = mask_shift ? (1u << mask_shift) - 1u : 0xffffffffu;
     k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, key_mask,
-                                                              ranges);
+                                                              ranges, n_views, n_tiles);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t take_status_sort(unsigned *bits, cudaStream_t s) {
+#if CS_CHECKED
+    unsigned v = 0;
+    const unsigned zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_status_sort, sizeof v, 0, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_status_sort, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) *bits |= v;
+    return e;
+#else
+    (void)bits;
+    (void)s;
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace cs

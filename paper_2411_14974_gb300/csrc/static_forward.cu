@@ -152,17 +152,19 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const int mask_shift = local_bits + BLOCK_MASK_BITS <= 32 ? local_bits : 0;
     if (e == cudaSuccess)
         e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, bboxes, R, local_bits,
-                              mask_shift, pk, pv, stream);
+                              mask_shift, pk, pv, stream, (uint32_t)P);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);
     const uint32_t *keys = in_b ? pk2 : pk;
     const uint32_t *vals = in_b ? pv2 : pv;
     if (e == cudaSuccess)
-        e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, mask_shift, ranges, tiles, stream);
+        e = launch_tile_ranges(keys, (int64_t)P, views_dev, local_bits, mask_shift, ranges, tiles, stream, 1);
     if (e == cudaSuccess) {
         BlendArgs a{views_dev, 1, ranges, vals, records, bboxes, s, tiles, scene->k, keys, mask_shift};
+        a.n_pairs = (uint32_t)P;
+        a.n_records = (uint32_t)R;
         e = launch_blend_forward(a, stream);
     }
     if (e != cudaSuccess) return fail_cuda(e, "cs_forward_static");
-    return CS_OK;
+    return take_device_status(stream, "cs_forward_static");
 }

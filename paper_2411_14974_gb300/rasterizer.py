@@ -485,6 +485,14 @@ def launch_count() -> int:
     return int(B.lib().cs_kernel_launch_count())
 
 
+def alu_rates(device: int = 0) -> dict:
+    """Measured per-SM rates of the transcendental unit (ex2.approx results per clock) and the FP32
+    pipe (fused multiply-adds per clock), the SM clock during the measurement and the SM count."""
+    out = (ctypes.c_double * 4)()
+    B.check(B.lib().cs_measure_alu_rates(int(device), out), "cs_measure_alu_rates")
+    return dict(mufu_per_clk_sm=out[0], fma_per_clk_sm=out[1], sm_mhz=out[2], sms=int(out[3]))
+
+
 WORK_FIELDS = ("visited", "lines_visited", "passed", "lines_passed", "contributing", "pixels")
 
 
@@ -579,9 +587,10 @@ class Server:
         return out
 
     def stats(self) -> dict:
-        a = (ctypes.c_uint64 * 6)()
+        a = (ctypes.c_uint64 * 7)()
         B.check(B.lib().cs_server_stats(self.handle, a), "cs_server_stats")
-        return dict(completed=a[0], batches=a[1], largest_batch=a[2], peak_bytes=a[3], queued=a[4], on_gpu=a[5])
+        return dict(completed=a[0], batches=a[1], largest_batch=a[2], peak_bytes=a[3], queued=a[4], on_gpu=a[5],
+                    peak_pool_bytes=a[6])
 
     def close(self):
         if self.handle:

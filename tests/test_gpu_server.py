@@ -97,6 +97,7 @@ def test_requests_arriving_while_batches_run_are_admitted():
     assert len(done) == len(reqs) and all(d["status"] == "ok" for d in done)
     assert st["batches"] >= 10 and st["largest_batch"] <= 4
     assert st["peak_bytes"] <= 40 << 20
+    assert 0 < st["peak_pool_bytes"] <= 40 << 20  # what the pool really held, not only the estimate
     assert all(d["latency_ms"] >= d["queue_ms"] >= 0 for d in done)
 
 
