@@ -71,7 +71,7 @@ typedef struct {
 
 /* Compositing constants.  The paper's Eq. 5 has none; these follow the 3DGS tile rasterizer the
    paper builds on (Sec. 3.2).  cs_default_settings(): tau = 1/255, alpha_max = 0.99,
-   t_min = 1e-4, bg = 0, dist_mode = 0, dist_power = 1, tile_test = 0. */
+   t_min = 1e-4, bg = 0, dist_mode = 0, dist_power = 1, tile_test = 0, tile_split = 0. */
 typedef struct {
     float tau;          /* pairs with alpha < tau add nothing; 0 <= tau < 1 */
     float alpha_max;    /* alpha = min(alpha_max, o I); 0 < alpha_max <= 1 */
@@ -82,6 +82,13 @@ typedef struct {
     int32_t tile_test;  /* 0: a convex covers every tile of its conservative rectangle; 1: only the
                            tiles an exact separating-axis test against its offset hull keeps (fewer
                            pairs, more work per convex; see the tile-range notes of cs_forward) */
+    int32_t tile_split; /* 0: one CTA blends each tile.  N in 256..2^24: a tile with more than N
+                           pairs is blended as chunks of N pairs by separate CTAs, merged in depth
+                           order by C = C_a + T_a C_b, T = T_a T_b, with the chunk in which a
+                           pixel's walk stops (T < t_min) walked again from T_a, so the image is
+                           that of the unsplit walk; the backward runs per chunk from the merged
+                           state.  Costs one more host synchronisation per forward and 5 KB of
+                           state per chunk of a heavy tile.  Ignored by cs_forward_static. */
 } cs_settings;
 
 /* How delta, sigma and opacity are given (Sec. 3.3 optimises them through activations). */
@@ -322,8 +329,8 @@ cs_status cs_refine(cs_context *ctx, int64_t n, int32_t k, int32_t sh_degree, co
    budget; requests that arrive while earlier batches are on the GPU join the next batch as soon
    as memory frees up.  A batch is preprocessed, binned and sorted as one (the view index lives in
    the tile key), then blended view by view, cheapest view first; each request completes as soon
-   as its own view's blend has run.  Batches alternate between two streams, so the preprocess and
-   sorts of one overlap the blends of the previous one.  Each view's image is identical to
+   as its own view's blend has run.  Batches alternate between two streams, at most one in flight
+   on each, so the preprocess and sorts of one overlap the blends of the previous one.  Each view's image is identical to
    rendering it alone with cs_forward.
    Images are written to caller-owned device buffers [3][H][W] that must stay alive until the
    request's completion has been polled.  All calls are thread-safe. */
@@ -344,6 +351,12 @@ cs_status cs_server_create(int32_t device, size_t memory_budget_bytes, int32_t m
                            cs_server **out);
 /* Stops the worker after the queued requests complete, then frees the server. */
 void cs_server_destroy(cs_server *srv);
+/* on = 1 (the default): the worker admits the next batch while earlier ones are still on the GPU
+   (two streams).  on = 0: the worker waits for each batch to finish on the GPU before it admits
+   the next, so batches never overlap; with max_batch = 1 that is plain one-view-at-a-time
+   rendering, the baseline the serving measurements compare against.  Applies from the next
+   batch on. */
+cs_status cs_server_set_pipelining(cs_server *srv, int32_t on);
 /* Registers a resident scene (device pointers as for cs_forward; the caller keeps them alive and
    unchanged while the scene is registered).  Returns its id in *scene_id. */
 cs_status cs_server_add_scene(cs_server *srv, const cs_scene *scene, int32_t *scene_id);

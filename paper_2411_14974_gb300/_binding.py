@@ -16,7 +16,7 @@ class CsCamera(ctypes.Structure):
 class CsSettings(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("alpha_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("dist_mode", ctypes.c_int32), ("dist_power", ctypes.c_float),
-                ("tile_test", ctypes.c_int32)]
+                ("tile_test", ctypes.c_int32), ("tile_split", ctypes.c_int32)]
 
 
 class CsScene(ctypes.Structure):
@@ -88,6 +88,7 @@ _PROTOTYPES = {
     "cs_server_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_size_t, ctypes.c_int32,
                                         ctypes.POINTER(CsSettings), ctypes.POINTER(_P)]),
     "cs_server_destroy": (None, [_P]),
+    "cs_server_set_pipelining": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cs_server_add_scene": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(ctypes.c_int32)]),
     "cs_server_remove_scene": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cs_server_submit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(CsCamera), _P,

@@ -112,6 +112,7 @@ extern "C" void cs_default_settings(cs_settings *s) {
     s->dist_mode = 0;
     s->dist_power = 1.0f;
     s->tile_test = 0;
+    s->tile_split = 0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -151,7 +152,7 @@ extern "C" cs_status cs_context_create(int32_t device, cs_context **out) {
     }
     uint64_t keep = UINT64_MAX;  // keep freed memory in the pool: later calls reuse it without the driver
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    e = cudaMallocHost(&c->host_total, sizeof(unsigned long long) * 2);
+    e = cudaMallocHost(&c->host_total, sizeof(unsigned long long) * 8);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->totals_ready, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->host_total) cudaFreeHost(c->host_total);
@@ -227,6 +228,8 @@ cs_status cs::check_settings(const cs_settings *st) {
     if (!(st->t_min >= 0.f && st->t_min < 1.f)) return fail(CS_ERR_ARG, "t_min must be in [0, 1)");
     if (st->dist_mode != 0 && st->dist_mode != 1) return fail(CS_ERR_ARG, "dist_mode must be 0 or 1");
     if (st->tile_test != 0 && st->tile_test != 1) return fail(CS_ERR_ARG, "tile_test must be 0 or 1");
+    if (st->tile_split != 0 && (st->tile_split < 256 || st->tile_split > (1 << 24)))
+        return fail(CS_ERR_ARG, "tile_split must be 0 or in 256..2^24 pairs");
     const float p = st->dist_power;
     if (!(p == 0.f || p == 0.5f || p == 1.f || p == 2.f)) return fail(CS_ERR_ARG, "dist_power must be 0, 0.5, 1 or 2");
     for (int i = 0; i < 3; ++i)
@@ -281,6 +284,7 @@ Settings cs::to_settings(const cs_settings &s) {
     o.bg[0] = s.bg[0]; o.bg[1] = s.bg[1]; o.bg[2] = s.bg[2];
     o.dist_mode = s.dist_mode; o.dist_power = s.dist_power;
     o.tile_test = s.tile_test;
+    o.tile_split = s.tile_split;
     return o;
 }
 
@@ -313,8 +317,24 @@ void cs::state_free(cs_fwd_state *s) {
     pool_free(s->ranges, st);
     pool_free(s->n_last, st);
     pool_free(s->t_final_own, st);
+    pool_free(s->split_items, st);
+    pool_free(s->split_heavy, st);
+    pool_free(s->split_slot, st);
+    pool_free(s->chunk_state, st);
     cudaSetDevice(prev);
     delete s;
+}
+
+// the tile-split fields of the blend arguments, from a forward state (none when not split)
+static void set_split_args(BlendArgs &a, const cs_fwd_state *s) {
+    if (!s->split_items) return;
+    a.split = (uint32_t)s->st.tile_split;
+    a.split_items = s->split_items;
+    a.n_items = s->n_items;
+    a.split_heavy = s->split_heavy;
+    a.n_heavy = s->n_heavy;
+    a.split_slot = s->split_slot;
+    a.chunk_state = s->chunk_state;
 }
 
 static int bits_for(uint64_t n) {
@@ -499,13 +519,64 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
                                   stream, V),
                "tile ranges");
     }
+    if (s->st.tile_split > 0 && P > 0) {
+        // tile split: which tiles are heavy, their chunk slots, the work items; the totals size the
+        // items and the chunk states, so they are read back (a second host synchronisation)
+        StageTimer tm(ctx, CS_STAGE_TILE_SORT, stream);
+        const uint32_t split = (uint32_t)s->st.tile_split;
+        uint32_t *heavy = nullptr, *light = nullptr, *heavy_base = nullptr, *light_base = nullptr;
+        unsigned long long *tot = nullptr, *stmp = nullptr;
+        unsigned int *cnt = nullptr;
+        cudaError_t e = pool_alloc(ctx, (void **)&heavy, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&light, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&heavy_base, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&light_base, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&tot, 2 * sizeof(unsigned long long), stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&cnt, 2 * sizeof(unsigned int), stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&stmp, scan_tmp_words(tiles) * 8, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&s->split_slot, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), stream);
+        if (e == cudaSuccess) e = launch_split_count(s->ranges, tiles, split, heavy, light, cnt, stream);
+        if (e == cudaSuccess) e = launch_exclusive_scan(heavy, nullptr, heavy_base, tiles, tot, stmp, stream);
+        if (e == cudaSuccess) e = launch_exclusive_scan(light, nullptr, light_base, tiles, tot + 1, stmp, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->host_total, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->host_total + 2, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->totals_ready, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ctx->totals_ready);
+        uint64_t n_slots = 0, n_light = 0, n_heavy = 0;
+        if (e == cudaSuccess) {
+            n_slots = ctx->host_total[0];
+            n_light = ctx->host_total[1];
+            n_heavy = (uint64_t)(*reinterpret_cast<const unsigned int *>(ctx->host_total + 2));
+            s->n_items = (uint32_t)(n_slots + n_light);
+            s->n_heavy = (uint32_t)n_heavy;
+            e = pool_alloc(ctx, (void **)&s->split_items, (size_t)s->n_items * sizeof(uint2), stream);
+        }
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&s->split_heavy, (size_t)(n_heavy + 1) * sizeof(uint2), stream);
+        if (e == cudaSuccess)
+            e = pool_alloc(ctx, (void **)&s->chunk_state, (size_t)(n_slots + 1) * SPLIT_STATE_FLOATS * 4, stream);
+        if (e == cudaSuccess)
+            e = launch_split_items(s->ranges, tiles, split, heavy_base, light_base, (uint32_t)n_slots, s->split_items,
+                                   s->split_heavy, cnt + 1, s->split_slot, stream);
+        pool_free(heavy, stream);
+        pool_free(light, stream);
+        pool_free(heavy_base, stream);
+        pool_free(light_base, stream);
+        pool_free(tot, stream);
+        pool_free(cnt, stream);
+        pool_free(stmp, stream);
+        CS_TRY(e, "tile split plan");
+    }
     {
         StageTimer tm(ctx, CS_STAGE_BLEND, stream);
         BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, tiles, s->k,
                     s->pair_keys, s->mask_shift};
         a.n_pairs = (uint32_t)P;
         a.n_records = (uint32_t)R;
-        if (s->view_done.size() == (size_t)V) {
+        set_split_args(a, s);
+        if (s->view_done.size() == (size_t)V && !a.split) {
             for (int v = 0; v < V; ++v) {  // one launch per view, each view's completion recorded
                 const ViewDesc &vd = s->views[v];
                 BlendArgs av = a;
@@ -516,6 +587,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             }
         } else {
             CS_TRY(launch_blend_forward(a, stream), "blend");
+            for (size_t v = 0; v < s->view_done.size(); ++v)  // every view is complete at once
+                CS_TRY(cudaEventRecord(s->view_done[v], stream), "record view");
         }
     }
     for (int v = 0; v < V; ++v) {
@@ -626,6 +699,7 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
                         s->pair_keys, s->mask_shift};
             a.n_pairs = (uint32_t)s->n_pairs;
             a.n_records = (uint32_t)s->n_records;
+            set_split_args(a, s);
             const int64_t stride = (int64_t)3 * s->views[0].width * s->views[0].height;
             e = launch_blend_backward(a, dL_dimage, stride, grads, stream);
         }

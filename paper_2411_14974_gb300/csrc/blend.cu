@@ -356,41 +356,32 @@ __device__ __forceinline__ void tile_of(const ViewDesc &vd, uint32_t g, int &tx,
     ty = (int)(local / (uint32_t)vd.tiles_x);
 }
 
-template <bool COUNT, int K>
-__global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, unsigned long long *counts) {
-    __shared__ float4 srec[FWD_THREADS / 32][STAGE_F4<K>];
-    __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
-    const uint32_t g = a.tile_offset + blockIdx.x;
-    const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
-    int tx, ty;
-    tile_of(vd, g, tx, ty);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
-    const int px = bx + (lane & 7), py = by + (lane >> 3);
-    const bool inside = px < vd.width && py < vd.height;
-    const float ox = (float)bx, oy = (float)by;
-    const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;
-    uint2 range = a.ranges[g];
-    if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
-    const Settings st = a.st;
-    float4 *wrec = srec[w];
-    uint32_t *sidx = sidx_all[w];
+// per-lane state of the forward's pixel
+struct FwdPixel {
+    float T, C0, C1, C2;  // transmittance and colour so far
+    uint32_t last;        // pair index + 1 of the last contributing pair (0: none)
+    bool done;            // the pixel is outside the image, or its walk has ended
+};
 
-    float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
-    uint32_t pos = range.x;
-    while (pos < range.y) {
-        if (__all_sync(0xffffffffu, done)) break;
+// Walks pairs [lo, hi) of a tile front to back for the warp's 8x4 block (origin ox, oy; this lane
+// at (lx, ly) within it), compositing into each lane's pixel (Eq. 5 with the 3DGS cut-offs) until
+// its transmittance falls below t_min.  Warp-uniform; lanes that are done take no part.
+template <bool COUNT, int K>
+__device__ __forceinline__ void walk_forward(const BlendArgs &a, uint32_t lo, uint32_t hi, int w, int lane, float ox,
+                                             float oy, float lx, float ly, float4 *wrec, uint32_t *sidx, FwdPixel &q,
+                                             unsigned long long (&cnt)[NCOUNT]) {
+    const Settings &st = a.st;
+    uint32_t pos = lo;
+    while (pos < hi) {
+        if (__all_sync(0xffffffffu, q.done)) break;
         // this warp's 8x4 block is column w & 1, row w >> 1 of the tile: mask bit w
-        const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, 1u << w, range.x, range.y,
-                                                pos, sidx, lane);
+        const int nh = gather_candidates<false>(a, ox + 0.5f, ox + 7.5f, oy + 0.5f, oy + 3.5f, 1u << w, lo, hi, pos,
+                                                sidx, lane);
         const uint32_t rl = copy_records<K>(wrec, a.records, a.pair_vals, sidx, nh, lane, a.n_records);
         const bool pass = stage_record<4, K>(wrec, lane, nh, rl, ox, oy, st);
         __syncwarp();
         uint32_t bits = __ballot_sync(0xffffffffu, pass);
-        if (!done) {
+        if (!q.done) {
             // two records per iteration: their evaluations are independent (only the compositing
             // depends on the record in front), which doubles the work between dependent latencies
             while (bits) {
@@ -409,27 +400,27 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
                 }
                 if (code1 == 2) {
                     const float4 c = rec1[1];
-                    const float wgt = p1.alpha * T;
-                    C0 = fmaf(wgt, c.x, C0);
-                    C1 = fmaf(wgt, c.y, C1);
-                    C2 = fmaf(wgt, c.z, C2);
-                    T = T * (1.0f - p1.alpha);
-                    last = sidx[j1] + 1;
-                    if (T < st.t_min) {
-                        done = true;
+                    const float wgt = p1.alpha * q.T;
+                    q.C0 = fmaf(wgt, c.x, q.C0);
+                    q.C1 = fmaf(wgt, c.y, q.C1);
+                    q.C2 = fmaf(wgt, c.z, q.C2);
+                    q.T = q.T * (1.0f - p1.alpha);
+                    q.last = sidx[j1] + 1;
+                    if (q.T < st.t_min) {
+                        q.done = true;
                         break;
                     }
                 }
                 if (code2 == 2) {
                     const float4 c = rec2[1];
-                    const float wgt = p2.alpha * T;
-                    C0 = fmaf(wgt, c.x, C0);
-                    C1 = fmaf(wgt, c.y, C1);
-                    C2 = fmaf(wgt, c.z, C2);
-                    T = T * (1.0f - p2.alpha);
-                    last = sidx[j2] + 1;
-                    if (T < st.t_min) {
-                        done = true;
+                    const float wgt = p2.alpha * q.T;
+                    q.C0 = fmaf(wgt, c.x, q.C0);
+                    q.C1 = fmaf(wgt, c.y, q.C1);
+                    q.C2 = fmaf(wgt, c.z, q.C2);
+                    q.T = q.T * (1.0f - p2.alpha);
+                    q.last = sidx[j2] + 1;
+                    if (q.T < st.t_min) {
+                        q.done = true;
                         break;
                     }
                 }
@@ -437,13 +428,146 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
         }
         __syncwarp();
     }
+}
+
+// Tile split (tile_split = N > 0).  A tile with more than N pairs is heavy: its list is cut into
+// chunks of N pairs, blended by separate CTAs (MODE_CHUNK) from T = 1 into a per-pixel chunk
+// state, then merged by one CTA per heavy tile (MODE_MERGE) in depth order:
+//     C = C_a + T_a C_b,  T = T_a T_b
+// A chunk's own walk stops once its local transmittance falls below t_min, which is safe (the
+// global transmittance is at most the local one).  Where T_a T_b < t_min the whole walk stops
+// inside chunk b: the merge walks that chunk again from T_a for those pixels, so the cut-off is
+// exactly the one of the unsplit walk.  The merge then leaves, for each chunk, the transmittance
+// after it and the colour behind it (the backward's starting point for that chunk).
+// Chunk state: [slot][5][256] floats, word 0-2 colour, 3 transmittance, 4 last pair + 1, for the
+// tile pixel with index split_pixel(x, y) (x, y within the tile).
+constexpr int MODE_PLAIN = 0, MODE_CHUNK = 1, MODE_MERGE = 2;
+constexpr int STATE_WORDS = 5;
+constexpr uint32_t NO_SLOT = 0xffffffffu;
+
+__device__ __forceinline__ int split_pixel(int x, int y) {
+    return 32 * ((x >> 3) + 2 * (y >> 2)) + (x & 7) + 8 * (y & 3);  // the forward's thread of the pixel
+}
+__device__ __forceinline__ float *state_word(const BlendArgs &a, uint32_t slot, int word, int pix) {
+    return a.chunk_state + ((size_t)slot * STATE_WORDS + word) * (TILE * TILE) + pix;
+}
+
+template <bool COUNT, int K, int MODE>
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, unsigned long long *counts) {
+    __shared__ float4 srec[FWD_THREADS / 32][STAGE_F4<K>];
+    __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
+    uint32_t g, chunk = 0, slot = NO_SLOT;
+    if (MODE == MODE_PLAIN) {
+        g = a.tile_offset + blockIdx.x;
+    } else {
+        const uint2 it = (MODE == MODE_CHUNK ? a.split_items : a.split_heavy)[blockIdx.x];
+        g = it.x;
+        if (MODE == MODE_CHUNK) {
+            chunk = it.y;
+            slot = a.split_slot[g];
+        } else {
+            slot = it.y;
+        }
+    }
+    const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
+    int tx, ty;
+    tile_of(vd, g, tx, ty);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const bool inside = px < vd.width && py < vd.height;
+    const float ox = (float)bx, oy = (float)by;
+    const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;
+    uint2 range = a.ranges[g];
+    if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
+    const Settings st = a.st;
+    float4 *wrec = srec[w];
+    uint32_t *sidx = sidx_all[w];
+
+    FwdPixel q{1.0f, 0.f, 0.f, 0.f, 0u, !inside};
+    unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, inside ? 1ull : 0ull};
+    const int sp = threadIdx.x;  // == split_pixel of this thread's pixel
+    if (MODE == MODE_MERGE) {
+        const uint32_t nch = (range.y - range.x + a.split - 1) / a.split;
+        // pass A, front to back over the chunks: the global state before each chunk (kept in word
+        // 3 for pass B), and the chunk in which the walk stops, if any
+        int stop = -1;
+        float Cs0 = 0.f, Cs1 = 0.f, Cs2 = 0.f;  // colour before the stop chunk
+        for (uint32_t c = 0; c < nch; ++c) {
+            const float cc0 = *state_word(a, slot + c, 0, sp), cc1 = *state_word(a, slot + c, 1, sp);
+            const float cc2 = *state_word(a, slot + c, 2, sp), tc = *state_word(a, slot + c, 3, sp);
+            const uint32_t lc = __float_as_uint(*state_word(a, slot + c, 4, sp));
+            *state_word(a, slot + c, 3, sp) = q.T;
+            if (stop >= 0) continue;
+            if (c == 0 || q.T * tc >= st.t_min) {  // chunk 0 starts at T = 1: its walk is the global one
+                q.C0 = fmaf(q.T, cc0, q.C0);
+                q.C1 = fmaf(q.T, cc1, q.C1);
+                q.C2 = fmaf(q.T, cc2, q.C2);
+                q.T *= tc;
+                if (lc) q.last = lc;
+                if (c == 0 && tc < st.t_min) stop = 0;
+            } else {
+                stop = (int)c;  // q holds the state before chunk c
+                Cs0 = q.C0;
+                Cs1 = q.C1;
+                Cs2 = q.C2;
+            }
+        }
+        if (!inside) stop = -1;
+        // walk again, from the state before it, the chunk in which each pixel's walk stops
+        for (uint32_t c = 1; c < nch; ++c) {
+            if (!__any_sync(0xffffffffu, stop == (int)c)) continue;
+            FwdPixel r = q;
+            r.done = stop != (int)c;
+            const uint32_t lo = range.x + c * a.split, hi = min(range.y, lo + a.split);
+            walk_forward<false, K>(a, lo, hi, w, lane, ox, oy, lx, ly, wrec, sidx, r, cnt);
+            if (stop == (int)c) q = r;
+        }
+        // pass B, back to front: per chunk the transmittance after it and the colour behind it
+        float A0 = q.T * st.bg[0], A1 = q.T * st.bg[1], A2 = q.T * st.bg[2];
+        float Tnext = q.T;
+        for (int c = (int)nch - 1; c >= 0; --c) {
+            const float cc0 = *state_word(a, slot + c, 0, sp), cc1 = *state_word(a, slot + c, 1, sp);
+            const float cc2 = *state_word(a, slot + c, 2, sp), tb = *state_word(a, slot + c, 3, sp);
+            const bool visited = stop < 0 || c <= stop;
+            *state_word(a, slot + c, 0, sp) = visited ? A0 : q.T * st.bg[0];
+            *state_word(a, slot + c, 1, sp) = visited ? A1 : q.T * st.bg[1];
+            *state_word(a, slot + c, 2, sp) = visited ? A2 : q.T * st.bg[2];
+            *state_word(a, slot + c, 3, sp) = visited ? Tnext : q.T;
+            if (c == stop) {  // its contribution: what the walk added from the state before it
+                A0 += q.C0 - Cs0;
+                A1 += q.C1 - Cs1;
+                A2 += q.C2 - Cs2;
+            } else if (visited) {
+                A0 = fmaf(tb, cc0, A0);
+                A1 = fmaf(tb, cc1, A1);
+                A2 = fmaf(tb, cc2, A2);
+            }
+            if (visited) Tnext = tb;
+        }
+    } else {
+        uint32_t lo = range.x, hi = range.y;
+        if (MODE == MODE_CHUNK && slot != NO_SLOT) {
+            lo = range.x + chunk * a.split;
+            hi = min(range.y, lo + a.split);
+        }
+        walk_forward<COUNT, K>(a, lo, hi, w, lane, ox, oy, lx, ly, wrec, sidx, q, cnt);
+        if (MODE == MODE_CHUNK && slot != NO_SLOT) {
+            *state_word(a, slot + chunk, 0, sp) = q.C0;
+            *state_word(a, slot + chunk, 1, sp) = q.C1;
+            *state_word(a, slot + chunk, 2, sp) = q.C2;
+            *state_word(a, slot + chunk, 3, sp) = q.T;
+            *state_word(a, slot + chunk, 4, sp) = __uint_as_float(q.last);
+            return;
+        }
+    }
     if (inside) {
         const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)py * vd.width + px;
-        vd.image[pix] = fmaf(T, st.bg[0], C0);
-        vd.image[hw + pix] = fmaf(T, st.bg[1], C1);
-        vd.image[2 * hw + pix] = fmaf(T, st.bg[2], C2);
-        if (vd.t_final) vd.t_final[pix] = T;
-        vd.n_last[pix] = last;
+        vd.image[pix] = fmaf(q.T, st.bg[0], q.C0);
+        vd.image[hw + pix] = fmaf(q.T, st.bg[1], q.C1);
+        vd.image[2 * hw + pix] = fmaf(q.T, st.bg[2], q.C2);
+        if (vd.t_final) vd.t_final[pix] = q.T;
+        vd.n_last[pix] = q.last;
     }
     if (COUNT) flush_counts(counts, cnt);
 }
@@ -597,13 +721,21 @@ __device__ __forceinline__ float reduce_words(float (&v)[N], int lane) {
     }
 }
 
-template <bool COUNT, int K>
+template <bool COUNT, int K, int MODE>
 __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
     __shared__ float4 srec[BWD_THREADS / 32][STAGE_F4<K>];
     __shared__ uint32_t sidx_all[BWD_THREADS / 32][32];
-    const uint32_t g = a.tile_offset + blockIdx.x;
+    uint32_t g, chunk = 0, slot = NO_SLOT;
+    if (MODE == MODE_PLAIN) {
+        g = a.tile_offset + blockIdx.x;
+    } else {  // a chunk of a heavy tile (see the tile split of the forward), or a whole light tile
+        const uint2 it = a.split_items[blockIdx.x];
+        g = it.x;
+        chunk = it.y;
+        slot = a.split_slot[g];
+    }
     const int v = find_view(a.views, a.n_views, g);
     const ViewDesc &vd = a.views[v];
     int tx, ty;
@@ -616,6 +748,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
     const Settings st = a.st;
     uint2 range = a.ranges[g];
     if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
+    if (MODE == MODE_CHUNK && slot != NO_SLOT) {  // this chunk's pairs only
+        range.x += chunk * a.split;
+        range.y = min(range.y, range.x + a.split);
+    }
     float4 *wrec = srec[w];
     uint32_t *sidx = sidx_all[w];
 
@@ -643,6 +779,16 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
         // colour seen behind the current pair (T_after times its colour, summed from the back),
         // kept as its product with dL/dC; it starts with the background
         q.GS[k] = q.Tc[k] * fmaf(q.G2[k], st.bg[2], fmaf(q.G1[k], st.bg[1], q.G0[k] * st.bg[0]));
+        if (MODE == MODE_CHUNK && slot != NO_SLOT) {
+            // a chunk of a heavy tile starts from the transmittance after it and the colour behind
+            // it, left by the forward's merge; its walk covers its own pairs only
+            const int spx = split_pixel(bx - tx * TILE + (lane & 7), by - ty * TILE + (lane >> 3) + 4 * k);
+            q.Tc[k] = *state_word(a, slot + chunk, 3, spx);
+            q.GS[k] = fmaf(q.G2[k], *state_word(a, slot + chunk, 2, spx),
+                           fmaf(q.G1[k], *state_word(a, slot + chunk, 1, spx),
+                                q.G0[k] * *state_word(a, slot + chunk, 0, spx)));
+            q.last[k] = min(q.last[k], range.y);
+        }
         lmax = max(lmax, q.last[k]);
     }
     const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
@@ -688,12 +834,53 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
     if (COUNT) flush_counts(counts, cnt);
 }
 
+// tile split planning: chunks of each heavy tile, 1 for each light tile
+__global__ void k_split_count(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t split,
+                              uint32_t *__restrict__ heavy, uint32_t *__restrict__ light,
+                              unsigned int *__restrict__ n_heavy_tiles) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tiles) return;
+    const uint2 r = ranges[g];
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    const uint32_t h = len > split ? (len + split - 1) / split : 0u;
+    heavy[g] = h;
+    light[g] = h ? 0u : 1u;
+    const unsigned int nh = __reduce_add_sync(__activemask(), h ? 1u : 0u);
+    if (nh && (threadIdx.x & 31) == __ffs(__activemask()) - 1) atomicAdd(n_heavy_tiles, nh);
+}
+
+__global__ void k_split_items(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t split,
+                              const uint32_t *__restrict__ heavy_base, const uint32_t *__restrict__ light_base,
+                              uint32_t n_slots, uint2 *__restrict__ items, uint2 *__restrict__ heavy_list,
+                              unsigned int *__restrict__ heavy_fill, uint32_t *__restrict__ slot_of_tile) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tiles) return;
+    const uint2 r = ranges[g];
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    const uint32_t h = len > split ? (len + split - 1) / split : 0u;
+    if (h) {
+        const uint32_t base = heavy_base[g];
+        for (uint32_t c = 0; c < h; ++c) items[base + c] = make_uint2(g, c);
+        slot_of_tile[g] = base;
+        heavy_list[atomicAdd(heavy_fill, 1u)] = make_uint2(g, base);
+    } else {
+        items[n_slots + light_base[g]] = make_uint2(g, 0u);
+        slot_of_tile[g] = NO_SLOT;
+    }
+}
+
 }  // namespace
 
 template <int K>
 static void blend_forward_k(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
-    if (counts) k_blend_forward<true, K><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
-    else k_blend_forward<false, K><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
+    if (counts) {
+        k_blend_forward<true, K, MODE_PLAIN><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
+    } else if (a.split) {
+        if (a.n_items) k_blend_forward<false, K, MODE_CHUNK><<<a.n_items, FWD_THREADS, 0, s>>>(a, nullptr);
+        if (a.n_heavy) k_blend_forward<false, K, MODE_MERGE><<<a.n_heavy, FWD_THREADS, 0, s>>>(a, nullptr);
+    } else {
+        k_blend_forward<false, K, MODE_PLAIN><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
+    }
 }
 
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
@@ -707,7 +894,7 @@ cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned lo
         case 8: blend_forward_k<8>(a, s, counts); break;
         default: return cudaErrorInvalidValue;
     }
-    count_launches(1);
+    count_launches(a.split && !counts ? (a.n_heavy ? 2 : 1) : 1);
     return cudaGetLastError();
 }
 
@@ -715,9 +902,14 @@ template <int K>
 static void blend_backward_k(const BlendArgs &a, const float *dL_dimage, int64_t image_stride, float4 *grad_records,
                              cudaStream_t s, unsigned long long *counts) {
     if (counts)
-        k_blend_backward<true, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, counts);
+        k_blend_backward<true, K, MODE_PLAIN><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records,
+                                                                              counts);
+    else if (a.split)
+        k_blend_backward<false, K, MODE_CHUNK><<<a.n_items, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride,
+                                                                               grad_records, nullptr);
     else
-        k_blend_backward<false, K><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride, grad_records, nullptr);
+        k_blend_backward<false, K, MODE_PLAIN><<<a.n_tiles, BWD_THREADS, 0, s>>>(a, dL_dimage, image_stride,
+                                                                               grad_records, nullptr);
 }
 
 cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
@@ -734,6 +926,24 @@ cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
     (void)s;
     return cudaSuccess;
 #endif
+}
+
+cudaError_t launch_split_count(const uint2 *ranges, uint32_t n_tiles, uint32_t split, uint32_t *heavy, uint32_t *light,
+                               unsigned int *n_heavy_tiles, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    k_split_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, split, heavy, light, n_heavy_tiles);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_items(const uint2 *ranges, uint32_t n_tiles, uint32_t split, const uint32_t *heavy_base,
+                               const uint32_t *light_base, uint32_t n_slots, uint2 *items, uint2 *heavy_list,
+                               unsigned int *heavy_fill, uint32_t *slot_of_tile, cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    k_split_items<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, split, heavy_base, light_base, n_slots, items,
+                                                        heavy_list, heavy_fill, slot_of_tile);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,

@@ -12,7 +12,7 @@ struct cs_context {
     int device = 0;
     int sm_count = 0;
     cudaMemPool_t pool = nullptr;             // stream-ordered pool for every transient buffer
-    unsigned long long *host_total = nullptr; // pinned readback slot for the pair count
+    unsigned long long *host_total = nullptr; // pinned readback slots (8 words): the forward's totals
     cudaEvent_t totals_ready = nullptr;       // recorded after the readback of the forward's totals
     // stage profiling: events recorded on the launching stream around every stage
     bool profiling = false;
@@ -51,6 +51,12 @@ struct cs_fwd_state {
     // when not empty (one event per view): the forward blends view by view, in view order, and
     // records view_done[v] on the stream once view v's image is written
     std::vector<cudaEvent_t> view_done;
+    // tile split (settings.tile_split > 0): work items, heavy tiles, slots and chunk states, kept
+    // for the backward
+    uint2 *split_items = nullptr, *split_heavy = nullptr;
+    uint32_t *split_slot = nullptr;
+    float *chunk_state = nullptr;
+    uint32_t n_items = 0, n_heavy = 0;
 };
 
 namespace cs {

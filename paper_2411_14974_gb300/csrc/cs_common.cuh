@@ -55,6 +55,7 @@ struct Settings {
     int32_t dist_mode;
     float dist_power;
     int32_t tile_test;
+    int32_t tile_split;
 };
 
 __host__ __device__ inline uint32_t hull_pack_count(uint32_t packed) { return packed & 15u; }
@@ -168,7 +169,28 @@ struct BlendArgs {
     uint32_t tile_offset = 0;   // global index of the launch's first tile (its tiles: n_tiles from there)
     uint32_t n_pairs = 0xffffffffu;    // pair-list length and record count: bounds of the checked
     uint32_t n_records = 0xffffffffu;  // builds' index tests (all ones: unknown)
+    // tile split (split > 0 pairs per chunk): work items (tile, chunk) of the chunked launches,
+    // heavy tiles (tile, first slot) of the merge, each tile's first slot, the chunk states
+    uint32_t split = 0;
+    const uint2 *split_items = nullptr;
+    uint32_t n_items = 0;
+    const uint2 *split_heavy = nullptr;
+    uint32_t n_heavy = 0;
+    const uint32_t *split_slot = nullptr;
+    float *chunk_state = nullptr;
 };
+// Tile split planning: per tile, the chunks of a heavy tile (more than `split` pairs; 0 for a
+// light tile) into heavy[], 1 for a light tile into light[], and the number of heavy tiles added
+// to *n_heavy_tiles (zeroed by the caller)
+cudaError_t launch_split_count(const uint2 *ranges, uint32_t n_tiles, uint32_t split, uint32_t *heavy, uint32_t *light,
+                               unsigned int *n_heavy_tiles, cudaStream_t s);
+// work items: heavy chunks first, at slot heavy_base[g] + chunk, then light tiles at
+// n_slots + light_base[g]; heavy tiles listed (order free) with their first slot; per tile its
+// first slot (0xffffffff for a light tile).  *heavy_fill zeroed by the caller.
+cudaError_t launch_split_items(const uint2 *ranges, uint32_t n_tiles, uint32_t split, const uint32_t *heavy_base,
+                               const uint32_t *light_base, uint32_t n_slots, uint2 *items, uint2 *heavy_list,
+                               unsigned int *heavy_fill, uint32_t *slot_of_tile, cudaStream_t s);
+constexpr int SPLIT_STATE_FLOATS = 5 * 256;  // per chunk slot: 5 words for each pixel of a 16x16 tile
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,

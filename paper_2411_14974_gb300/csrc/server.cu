@@ -8,7 +8,8 @@
 //                    (smallest first), runs the batched forward (one preprocess, binning and sort
 //                    for all views, then one blend launch per view, each followed by that view's
 //                    completion event) on one of two streams and goes back for the next batch --
-//                    so the preprocess and sorts of batch k+1 overlap the blends of batch k;
+//                    so the preprocess and sorts of batch k+1 overlap the blends of batch k (at
+//                    most one batch in flight per stream);
 //   finisher         waits for the batches in order and, within a batch, for each view's event,
 //                    posting each request's completion as soon as its own image is written; then
 //                    frees the batch's buffers and returns its memory to the budget.
@@ -66,6 +67,7 @@ struct cs_server {
     int device = 0;
     size_t budget = 0;
     int max_batch = 1;
+    bool pipelined = true;  // false: each batch finishes on the GPU before the next is admitted
     cs_settings settings{};
     cs_context *ctx = nullptr;
     cudaStream_t streams[2] = {nullptr, nullptr};
@@ -124,6 +126,12 @@ void cs_server::run_worker() {
         cv_work.wait(lk, [&] { return stop || !pending.empty(); });
         if (pending.empty()) {
             if (stop) break;
+            continue;
+        }
+        // one batch in flight per stream: running further ahead cannot feed the GPU faster, it only
+        // holds memory (and makes the pool grow) while requests that could join a batch wait
+        if (inflight.size() >= 2) {
+            cv_mem.wait(lk);
             continue;
         }
         Batch *b = new (std::nothrow) Batch();
@@ -216,6 +224,7 @@ void cs_server::run_worker() {
             b->status = run_forward(ctx, s, stream);
         }
         if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess) cudaEventRecord(b->done, stream);
+        if (!pipelined) cudaStreamSynchronize(stream);  // no overlap between batches
 
         lk.lock();
         inflight.push_back(b);
@@ -360,6 +369,13 @@ extern "C" void cs_server_destroy(cs_server *srv) {
     cudaSetDevice(prev);
     cs_context_destroy(srv->ctx);
     delete srv;
+}
+
+extern "C" cs_status cs_server_set_pipelining(cs_server *srv, int32_t on) {
+    if (!srv) return fail(CS_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->pipelined = on != 0;
+    return CS_OK;
 }
 
 extern "C" cs_status cs_server_add_scene(cs_server *srv, const cs_scene *scene, int32_t *scene_id) {

@@ -33,6 +33,7 @@ class Settings:
     dist_mode: int = 0
     dist_power: float = 1.0
     tile_test: int = 0  # 1: exact tile test against the offset hull (tighter binning)
+    tile_split: int = 0  # N > 0: tiles with more than N pairs blended as chunks of N, then merged
 
     def struct(self) -> B.CsSettings:
         s = B.CsSettings()
@@ -41,6 +42,7 @@ class Settings:
             s.bg[i] = float(self.bg[i])
         s.dist_mode, s.dist_power = int(self.dist_mode), float(self.dist_power)
         s.tile_test = int(self.tile_test)
+        s.tile_split = int(self.tile_split)
         return s
 
 
@@ -538,18 +540,21 @@ class Server:
     """Continuous-batching view server over resident scenes (cs_server_* in the C ABI).
 
     Requests are queued with submit(); a worker thread in the library admits them into batches
-    by an estimated memory budget and renders each batch with one binning/sort and one blend
-    launch; poll() returns completions with their latencies."""
+    by a memory budget and renders each batch with one preprocess, binning and sort and one blend
+    launch per view; poll() returns completions with their latencies.  pipelined=False makes the
+    worker wait for each batch before admitting the next (with max_batch=1: one view at a time)."""
 
     STATUS = {0: "ok", 1: "arg", 2: "cuda", 3: "nomem", 4: "budget", 5: "timeout", 6: "device", 7: "state"}
 
     def __init__(self, device: int = 0, budget_bytes: int = 32 << 30, max_batch: int = 32,
-                 settings: Optional[Settings] = None):
+                 settings: Optional[Settings] = None, pipelined: bool = True):
         h = ctypes.c_void_p()
         s = (settings or Settings()).struct()
         B.check(B.lib().cs_server_create(int(device), int(budget_bytes), int(max_batch), ctypes.byref(s),
                                          ctypes.byref(h)), "cs_server_create")
         self.handle = h
+        if not pipelined:
+            B.check(B.lib().cs_server_set_pipelining(h, 0), "cs_server_set_pipelining")
         self.device = device
         self._scenes = {}
         self._outputs = {}

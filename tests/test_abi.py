@@ -70,3 +70,11 @@ def test_static_forward_reports_a_failed_runtime_call_on_cpu(library):
     code = lib.cs_forward_static(ctypes.byref(sc), ctypes.byref(cam), ctypes.byref(s), p, p, None)
     assert code == 2  # CS_ERR_CUDA
     assert len(lib.cs_last_error()) > 0
+
+
+def test_checked_library_builds_and_exports_every_declared_symbol():
+    """The bounds-checked variant (CS_CHECKED=1) links completely and loads without a GPU."""
+    path = b.build(checked=True)
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
