@@ -3,7 +3,8 @@
 
 One step = one pass of the whole differentiable rasterizer over one view: per-convex preprocess
 (projection, exact hull, lines, tile ranges, SH colour), depth sort, pair emission, tile sort,
-per-tile blend, per-tile reverse blend and the preprocess backward.  Workload: 1,000,000
+per-tile blend, per-tile reverse blend and the preprocess backward, which writes the gradients
+(cs_backward_write).  Workload: 1,000,000
 surface-clustered convexes (K = 6 points, SH degree 3, float32) rendered at 1920x1080, one view
 per step cycling over 4 cameras on a sphere of radius 4; the loss cotangent dL/dimage is a fixed
 random image.  Inputs are resident in HBM when the timed region starts and are larger than L2
@@ -238,7 +239,7 @@ def tile_test_bench(dev_index, sc, cams, steps, warmup):
 
         def step(i):
             _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
-            cs.backward(st, dL, grads)
+            cs.backward(st, dL, grads, accumulate=False)
             st.release()
 
         for i in range(warmup):
@@ -299,7 +300,7 @@ def light_bench(dev_index, sc, cams, steps, warmup):
 
     def fwd_bwd(i):
         _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
-        cs.backward(st, dL, grads)
+        cs.backward(st, dL, grads, accumulate=False)
         st.release()
 
     f_ms, f_bd = timed(fwd)
@@ -377,7 +378,7 @@ def stress_bench(dev_index, steps=3, warmup=2, tile_test=0, tile_split=0):
 
     def step():
         _, _, st = cs.forward(scene, cams, settings, keep_state=True, image=image)
-        cs.backward(st, dL, grads)
+        cs.backward(st, dL, grads, accumulate=False)
         return st
 
     for _ in range(warmup):
@@ -518,7 +519,7 @@ def run_ours(args):
 
     def step(i):
         _, _, st = cs.forward(scene, [cams[i % len(cams)]], settings, keep_state=True, image=image)
-        cs.backward(st, dL, grads)
+        cs.backward(st, dL, grads, accumulate=False)
         st.release()
 
     def barrier():
@@ -641,9 +642,10 @@ def run_ours(args):
         sh_w = 3 * (sc.sh_degree + 1) ** 2
         p_bytes = 4 * (sc.k * 3 + 3 + sh_w)
         pre_bytes = n_conv * (p_bytes + 128 + 4 + 4 + 8 + 16 + 4)
-        # backward: parameters, the record's first 32 bytes (hull), the 128-byte gradient record,
-        # points and SH gradients read and written back, delta / sigma / opacity gradients likewise
-        bwd_bytes = n_conv * (p_bytes + 32 + 128 + 2 * 4 * (sc.k * 3 + sh_w) + 3 * 4 * 2)
+        # backward (the step writes the gradients, cs_backward_write): parameters, the record's first
+        # 32 bytes (hull), the 128-byte gradient record, the points, SH, delta, sigma and opacity
+        # gradients written
+        bwd_bytes = n_conv * (p_bytes + 32 + 128 + 4 * (sc.k * 3 + sh_w) + 3 * 4)
         stages = {}
         stages["preprocess"] = dict(bound="hbm", bytes=pre_bytes, achieved_gbs=pre_bytes / (breakdown["preprocess"] / 1e3) / 1e9,
                                     peak_gbs=hbm)

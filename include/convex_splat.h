@@ -168,6 +168,13 @@ cs_status cs_forward(cs_context *ctx, const cs_scene *scene, const cs_camera *ca
 cs_status cs_backward(cs_context *ctx, const cs_fwd_state *state, const float *dL_dimage, float *dpoints,
                       float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream);
 
+/* cs_backward, except that the gradients are written instead of added to the buffers' contents:
+   the buffers need not be cleared first (with several views the call clears them, then adds the
+   views' contributions).  With one view the preprocess backward then reads no old gradient, 264
+   of its 988 bytes per convex at K = 6 and SH degree 3.  Same arguments and errors. */
+cs_status cs_backward_write(cs_context *ctx, const cs_fwd_state *state, const float *dL_dimage, float *dpoints,
+                            float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream);
+
 /* Release a state (its device buffers return to the context's pool on the state's stream). */
 void cs_state_release(cs_fwd_state *state);
 

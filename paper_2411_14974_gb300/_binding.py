@@ -62,6 +62,7 @@ _PROTOTYPES = {
     "cs_forward": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera), ctypes.c_int32,
                                   ctypes.POINTER(CsSettings), _P, _P, ctypes.POINTER(_P), _P]),
     "cs_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cs_backward_write": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "cs_state_release": (None, [_P]),
     "cs_state_copy": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "cs_state_sizes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),

@@ -676,8 +676,21 @@ extern "C" cs_status cs_debug_set_pair_value(cs_fwd_state *s, int64_t index, uin
 #endif
 }
 
+static cs_status run_backward(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
+                              float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream_ptr, bool write);
+
 extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
                                  float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream_ptr) {
+    return run_backward(ctx, s, dL_dimage, dpoints, ddelta, dsigma, dopacity, dsh, stream_ptr, false);
+}
+
+extern "C" cs_status cs_backward_write(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
+                                       float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream_ptr) {
+    return run_backward(ctx, s, dL_dimage, dpoints, ddelta, dsigma, dopacity, dsh, stream_ptr, true);
+}
+
+static cs_status run_backward(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, float *dpoints,
+                              float *ddelta, float *dsigma, float *dopacity, float *dsh, void *stream_ptr, bool write) {
     if (!ctx || !s) return fail(CS_ERR_ARG, "context or state is NULL");
     if (s->ctx != ctx) return fail(CS_ERR_STATE, "state belongs to another context");
     if (!dL_dimage) return fail(CS_ERR_ARG, "dL_dimage is NULL");
@@ -688,6 +701,18 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
     const int V = (int)s->views.size();
     cs_status st_code = CS_OK;
     float4 *grads = nullptr;
+    if (write && (V > 1 || s->n_records == 0)) {
+        // several views add into shared gradients with atomics: clear them first
+        const int64_t n = s->scene.n;
+        const int64_t nb = (int64_t)(s->scene.sh_degree + 1) * (s->scene.sh_degree + 1);
+        cudaError_t e = cudaSuccess;
+        if (dpoints) e = cudaMemsetAsync(dpoints, 0, (size_t)n * s->k * 3 * 4, stream);
+        if (e == cudaSuccess && ddelta) e = cudaMemsetAsync(ddelta, 0, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dsigma) e = cudaMemsetAsync(dsigma, 0, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dopacity) e = cudaMemsetAsync(dopacity, 0, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dsh) e = cudaMemsetAsync(dsh, 0, (size_t)(n * nb * 3) * 4, stream);
+        if (e != cudaSuccess) return fail_cuda(e, "clear gradients");
+    }
     if (s->n_records == 0) return CS_OK;
     {
         cudaError_t e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);
@@ -706,6 +731,7 @@ extern "C" cs_status cs_backward(cs_context *ctx, const cs_fwd_state *s, const f
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_PREPROCESS_BACKWARD, stream);
             PreprocessGrads g{dpoints, ddelta, dsigma, dopacity, dsh};
+            g.write = write && V == 1;
             e = launch_preprocess_backward(s->views_dev, V, s->scene.n, s->k, s->scene.sh_degree, s->scene.storage,
                                            s->st, s->records, s->counts, grads, g, V > 1, stream);
         }

@@ -84,6 +84,7 @@ cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_h
 
 struct PreprocessGrads {
     float *dpoints, *ddelta, *dsigma, *dopacity, *dsh;
+    bool write = false;  // single view: write the gradients instead of adding them to the buffers
 };
 cudaError_t launch_preprocess_backward(const ViewDesc *views_dev, int n_views, int64_t max_n, int k, int sh_degree,
                                        int storage, const Settings &st, const float4 *records, const uint32_t *counts,

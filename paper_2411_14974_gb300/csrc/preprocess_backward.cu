@@ -36,11 +36,13 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
     if (i0 >= vd.n) return;
     const int cnt = (int)min((int64_t)PRE_THREADS, vd.n - i0);
     const int sh_stride = stage_sh<STG>(ssh, vd.sh, i0, cnt, SW);
-    if (!ATOMIC) {
+    if (!ATOMIC) {  // the gradients to add to: the buffers' contents, or zero when they are written
         if (out.dpoints)
-            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) s_dp[(q / PW) * PS + q % PW] = out.dpoints[i0 * PW + q];
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS)
+                s_dp[(q / PW) * PS + q % PW] = out.write ? 0.f : out.dpoints[i0 * PW + q];
         if (SEP_DSH && out.dsh)
-            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) s_dsh[(q / SW) * SS + q % SW] = out.dsh[i0 * SW + q];
+            for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS)
+                s_dsh[(q / SW) * SS + q % SW] = out.write ? 0.f : out.dsh[i0 * SW + q];
     }
     // slot of SH word w of this thread's convex in the staged buffer (binary32 words)
     auto sh_slot = [&](int w) -> float & {
@@ -65,9 +67,14 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
         prefetch_l2(pp);
         prefetch_l2(pp + PW * esz - 1);
     }
-    if (IN_PLACE && out.dsh)
+    if (IN_PLACE && out.dsh && !out.write)
         for (int q = threadIdx.x * 32; q < cnt * SW; q += PRE_THREADS * 32) prefetch_l2(out.dsh + i0 * SW + q);
     const bool live = i < vd.n && counts[rec] != 0;
+    if (!ATOMIC && out.write && i < vd.n && !live) {  // a convex that is not drawn: zero gradients
+        if (out.ddelta) out.ddelta[i] = 0.f;
+        if (out.dsigma) out.dsigma[i] = 0.f;
+        if (out.dopacity) out.dopacity[i] = 0.f;
+    }
     cp_async_wait_all();
     __syncthreads();  // staged SH (and, with one view, the gathered gradients) visible to the block
     if (!live && i < vd.n) zero_sh_slots();
@@ -174,6 +181,10 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
             if (out.ddelta && dd_delta != 0.f) atomicAdd(out.ddelta + i, dd_delta);
             if (out.dsigma && dd_sigma != 0.f) atomicAdd(out.dsigma + i, dd_sigma);
             if (out.dopacity && dd_opa != 0.f) atomicAdd(out.dopacity + i, dd_opa);
+        } else if (out.write) {
+            if (out.ddelta) out.ddelta[i] = dd_delta;
+            if (out.dsigma) out.dsigma[i] = dd_sigma;
+            if (out.dopacity) out.dopacity[i] = dd_opa;
         } else {
             if (out.ddelta) out.ddelta[i] += dd_delta;
             if (out.dsigma) out.dsigma[i] += dd_sigma;
@@ -294,7 +305,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
                 for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) {
                     const int t = q / SW;
                     const float d = sh_stride ? ssh[t * sh_stride * 4 + (q - t * SW)] : ssh[q];
-                    out.dsh[i0 * SW + q] += d;
+                    if (out.write) out.dsh[i0 * SW + q] = d;
+                    else out.dsh[i0 * SW + q] += d;
                 }
             } else {
                 for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS)

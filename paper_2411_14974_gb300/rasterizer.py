@@ -216,9 +216,10 @@ def forward(scene: SceneTensors, cams: Sequence, settings: Optional[Settings] = 
     return image, t_final, state
 
 
-def backward(state: State, dL_dimage: torch.Tensor, grads: Optional[dict] = None) -> dict:
+def backward(state: State, dL_dimage: torch.Tensor, grads: Optional[dict] = None, accumulate: bool = True) -> dict:
     """cs_backward: accumulate d(loss)/d(points, delta, sigma, opacity, sh) into ``grads``
-    (zero tensors are created when not given)."""
+    (zero tensors are created when not given); accumulate=False writes them instead
+    (cs_backward_write: the buffers' contents are not read)."""
     sc = state.scene
     if grads is None:  # gradients are float32 whatever the parameter storage
         z = lambda t: torch.zeros(t.shape, dtype=torch.float32, device=t.device)
@@ -227,10 +228,10 @@ def backward(state: State, dL_dimage: torch.Tensor, grads: Optional[dict] = None
     if g.dtype != torch.float32:
         g = g.float()
     ptr = lambda t: t.data_ptr() if (t is not None and t.numel()) else None
-    code = B.lib().cs_backward(state.ctx.handle, state.handle, g.data_ptr(), ptr(grads.get("points")),
-                               ptr(grads.get("delta")), ptr(grads.get("sigma")), ptr(grads.get("opacity")),
-                               ptr(grads.get("sh")), _stream_ptr(sc.points.device))
-    B.check(code, "cs_backward")
+    fn = B.lib().cs_backward if accumulate else B.lib().cs_backward_write
+    code = fn(state.ctx.handle, state.handle, g.data_ptr(), ptr(grads.get("points")), ptr(grads.get("delta")),
+              ptr(grads.get("sigma")), ptr(grads.get("opacity")), ptr(grads.get("sh")), _stream_ptr(sc.points.device))
+    B.check(code, "cs_backward" if accumulate else "cs_backward_write")
     return grads
 
 

@@ -259,3 +259,26 @@ def test_autograd_render_matches_direct_backward_after_buffers_are_freed():
         got = p.grad.detach().cpu().numpy().astype(np.float64)
         scale = np.abs(want[f]).max() + 1e-30
         assert np.abs(got - want[f]).max() <= 1e-5 * scale, f
+
+
+@pytest.mark.parametrize("n_views", [1, 2])
+def test_backward_write_equals_accumulate_into_zeros(n_views):
+    """cs_backward_write writes the gradients (buffers full of NaN beforehand) and equals
+    cs_backward accumulating into zeroed buffers, up to the order of the blend's atomics."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = syn.surface_scene(61, n=8_000, sh_degree=3)
+    cams = syn.sphere_cameras(n_views, 96, 72, 4.0, seed=62)
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    G = torch.as_tensor(np.random.default_rng(63).uniform(-1, 1, (n_views, 3, 72, 96)).astype(np.float32), device=dev)
+    _, _, state = cs.forward(t, cams, cs.Settings(), keep_state=True)
+    acc = cs.backward(state, G)
+    junk = {f: torch.full(tuple(getattr(t, f).shape), float("nan"), device=dev) for f in FIELDS}
+    wrote = cs.backward(state, G, junk, accumulate=False)
+    torch.cuda.synchronize()
+    state.release()
+    for f in FIELDS:
+        a, w = acc[f].cpu().numpy(), wrote[f].cpu().numpy()
+        assert np.isfinite(w).all(), f
+        assert np.abs(a - w).max() <= 1e-5 * (np.abs(a).max() + 1e-30), f
