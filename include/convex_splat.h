@@ -205,10 +205,14 @@ cs_status cs_state_copy(const cs_fwd_state *state, int32_t which, void *host_dst
 cs_status cs_state_sizes(const cs_fwd_state *state, int64_t *records, int64_t *pairs, int64_t *tiles);
 
 /* One forward (and, if dL_dimage_host is not NULL, backward) with every buffer in HOST memory
-   (preferably pinned): the scene arrays are copied to the device, rendered, and the image and
-   gradients copied back before the call returns.  Same layouts as cs_forward / cs_backward;
-   scene_host holds host pointers.  The gradients are written (not accumulated); any gradient
-   pointer may be NULL.  Device buffers come from the context's pool; the call synchronises. */
+   (preferably pinned): the scene arrays are copied to the device and rendered; the image,
+   dL_dimage and, with one view, the gradients are written and read in place by the kernels when
+   the device can reach the host buffers (pinned or registered memory, or any memory on a host
+   whose page tables the GPU uses, as a Grace host over NVLink-C2C), so that the gradients stream
+   out while they are computed; otherwise they go through device buffers and copies.  Same
+   layouts as cs_forward / cs_backward; scene_host holds host pointers.  The gradients are written
+   (not accumulated); any gradient pointer may be NULL.  Device buffers come from the context's
+   pool; the call synchronises. */
 cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_camera *cams, int32_t n_views,
                        const cs_settings *settings, const float *dL_dimage_host, float *image_host,
                        float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,

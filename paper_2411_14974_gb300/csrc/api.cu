@@ -805,6 +805,26 @@ extern "C" cs_status cs_state_copy(const cs_fwd_state *s, int32_t which, void *h
 // ---------------------------------------------------------------------------------------------
 // host-buffer step and work counters
 // ---------------------------------------------------------------------------------------------
+// the device address of host buffer p when kernels on `device` can read and write it in place:
+// pinned or registered memory, or any host memory where the GPU walks the host's page tables
+// (on a Grace host, over NVLink-C2C); NULL otherwise
+static void *device_view(const void *p, int device) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged)
+        return a.devicePointer ? a.devicePointer : const_cast<void *>(p);
+    if (a.type == cudaMemoryTypeUnregistered) {
+        int pageable = 0;
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device);
+        if (pageable) return const_cast<void *>(p);
+    }
+    return nullptr;
+}
+
 extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_camera *cams, int32_t n_views,
                                   const cs_settings *settings, const float *dL_host, float *image_host,
                                   float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,
@@ -820,37 +840,56 @@ extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_
     const size_t esz = sh->storage == CS_STORE_F32 ? 4 : 2;  // parameters as stored; gradients float32
     const size_t b_pts = (size_t)n * sh->k * 3, b_one = (size_t)n, b_sh = (size_t)n * nb * 3;
     const size_t b_img = (size_t)n_views * 3 * cams[0].width * cams[0].height * 4;
+    const bool bwd = dL_host != nullptr;
+    // The scene is copied to the device (the preprocess stages it with cp.async).  dL/dimage, the
+    // image and, with one view, the gradients are read and written in place by the kernels when
+    // the device can reach the host buffers, so the gradients stream out while the preprocess
+    // backward computes them; otherwise they go through device buffers and copies.
+    float *outs_host[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
+    float *dl_view = bwd ? static_cast<float *>(device_view(dL_host, ctx->device)) : nullptr;
+    float *img_view = static_cast<float *>(device_view(image_host, ctx->device));
+    float *g_view[5] = {};
+    bool grads_direct = bwd && n_views == 1;
+    for (int i = 0; i < 5; ++i) {
+        g_view[i] = static_cast<float *>(device_view(outs_host[i], ctx->device));
+        if (outs_host[i] && !g_view[i]) grads_direct = false;
+    }
     float *d[12] = {};
     const size_t sizes[12] = {b_pts * esz, b_one * esz, b_one * esz, b_one * esz, b_sh * esz, b_img,
                               b_img,       b_pts * 4,   b_one * 4,   b_one * 4,   b_one * 4, b_sh * 4};
-    const bool bwd = dL_host != nullptr;
-    const int nbuf = bwd ? 12 : 6;
+    bool need[12] = {true, true, true, true, true, !img_view, bwd && !dl_view};
+    for (int i = 7; i < 12; ++i) need[i] = bwd && !grads_direct;
     cs_fwd_state *state = nullptr;
     cs_status code = CS_OK;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < nbuf && e == cudaSuccess; ++i) e = pool_alloc(ctx, (void **)&d[i], sizes[i], stream);
+    for (int i = 0; i < 12 && e == cudaSuccess; ++i)
+        if (need[i]) e = pool_alloc(ctx, (void **)&d[i], sizes[i], stream);
     const void *srcs[5] = {sh->points, sh->delta, sh->sigma, sh->opacity, sh->sh};
     for (int i = 0; i < 5 && e == cudaSuccess; ++i)
         if (sizes[i]) e = cudaMemcpyAsync(d[i], srcs[i], sizes[i], cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && bwd) e = cudaMemcpyAsync(d[6], dL_host, b_img, cudaMemcpyHostToDevice, stream);
-    for (int i = 7; i < 12 && e == cudaSuccess && bwd; ++i) e = cudaMemsetAsync(d[i], 0, sizes[i], stream);
+    if (e == cudaSuccess && need[6]) e = cudaMemcpyAsync(d[6], dL_host, b_img, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) code = fail_cuda(e, "cs_step_host upload");
+    float *img = img_view ? img_view : d[5];
+    const float *dl = dl_view ? dl_view : d[6];
+    float *gout[5];
+    for (int i = 0; i < 5; ++i) gout[i] = grads_direct ? g_view[i] : (outs_host[i] ? d[7 + i] : nullptr);
     if (code == CS_OK) {
         cs_scene dev = *sh;
         dev.points = d[0]; dev.delta = d[1]; dev.sigma = d[2]; dev.opacity = d[3]; dev.sh = d[4];
-        code = cs_forward(ctx, &dev, cams, n_views, settings, d[5], nullptr, bwd ? &state : nullptr, stream_ptr);
-        if (code == CS_OK && bwd) code = cs_backward(ctx, state, d[6], d[7], d[8], d[9], d[10], d[11], stream_ptr);
+        code = cs_forward(ctx, &dev, cams, n_views, settings, img, nullptr, bwd ? &state : nullptr, stream_ptr);
+        if (code == CS_OK && bwd)
+            code = cs_backward_write(ctx, state, dl, gout[0], gout[1], gout[2], gout[3], gout[4], stream_ptr);
     }
     if (code == CS_OK) {
-        e = cudaMemcpyAsync(image_host, d[5], b_img, cudaMemcpyDeviceToHost, stream);
-        float *outs[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
-        for (int i = 0; i < 5 && e == cudaSuccess && bwd; ++i)
-            if (outs[i] && sizes[7 + i]) e = cudaMemcpyAsync(outs[i], d[7 + i], sizes[7 + i], cudaMemcpyDeviceToHost, stream);
+        if (!img_view) e = cudaMemcpyAsync(image_host, d[5], b_img, cudaMemcpyDeviceToHost, stream);
+        for (int i = 0; i < 5 && e == cudaSuccess && bwd && !grads_direct; ++i)
+            if (outs_host[i] && sizes[7 + i])
+                e = cudaMemcpyAsync(outs_host[i], d[7 + i], sizes[7 + i], cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) code = fail_cuda(e, "cs_step_host download");
     }
     if (state) state_free(state);
-    for (int i = 0; i < nbuf; ++i) pool_free(d[i], stream);
+    for (int i = 0; i < 12; ++i) pool_free(d[i], stream);
     return code;
 }
 

@@ -282,3 +282,34 @@ def test_backward_write_equals_accumulate_into_zeros(n_views):
         a, w = acc[f].cpu().numpy(), wrote[f].cpu().numpy()
         assert np.isfinite(w).all(), f
         assert np.abs(a - w).max() <= 1e-5 * (np.abs(a).max() + 1e-30), f
+
+
+@pytest.mark.parametrize("pinned,n_views", [(True, 1), (False, 1), (True, 2)])
+def test_step_through_host_buffers_equals_device_calls(pinned, n_views):
+    """cs_step_host (scene, dL/dimage, image and gradients in host memory; the gradients, image
+    and cotangent read and written in place where the GPU can reach them) gives the image of
+    cs_forward bit for bit and the gradients of cs_backward up to the order of the atomics."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    sc = syn.surface_scene(64, n=6_000, sh_degree=2)
+    cams = syn.sphere_cameras(n_views, 80, 64, 4.0, seed=65)
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    G = np.random.default_rng(66).uniform(-1, 1, (n_views, 3, 64, 80)).astype(np.float32)
+    img, _, state = cs.forward(t, cams, cs.Settings(), keep_state=True)
+    want = cs.backward(state, torch.as_tensor(G, device=dev))
+    torch.cuda.synchronize()
+    state.release()
+    host = lambda a: (torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory() if pinned
+                      else torch.as_tensor(np.ascontiguousarray(a, np.float32)))
+    scene_h = dict(points=host(sc.points), delta=host(sc.delta), sigma=host(sc.sigma), opacity=host(sc.opacity),
+                   sh=host(sc.sh))
+    img_h = host(np.full((n_views, 3, 64, 80), np.nan))
+    g_h = {f: host(np.full(tuple(getattr(t, f).shape), np.nan)) for f in FIELDS}
+    cs.step_host(scene_h, sc.sh_degree, cams, cs.Settings(), host(G), img_h, g_h)
+    torch.cuda.synchronize()
+    assert torch.equal(img_h, img.cpu())
+    for f in FIELDS:
+        a, b = g_h[f].numpy(), want[f].cpu().numpy()
+        assert np.isfinite(a).all(), f
+        assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-30), f
