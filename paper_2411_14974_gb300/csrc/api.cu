@@ -317,6 +317,7 @@ void cs::state_free(cs_fwd_state *s) {
     pool_free(s->ranges, st);
     pool_free(s->n_last, st);
     pool_free(s->t_final_own, st);
+    pool_free(s->tile_order, st);
     pool_free(s->split_items, st);
     pool_free(s->split_heavy, st);
     pool_free(s->split_slot, st);
@@ -327,6 +328,7 @@ void cs::state_free(cs_fwd_state *s) {
 
 // the tile-split fields of the blend arguments, from a forward state (none when not split)
 static void set_split_args(BlendArgs &a, const cs_fwd_state *s) {
+    a.tile_order = s->tile_order;
     if (!s->split_items) return;
     a.split = (uint32_t)s->st.tile_split;
     a.split_items = s->split_items;
@@ -518,6 +520,17 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(launch_tile_ranges(s->pair_keys, (int64_t)P, s->views_dev, local_bits, s->mask_shift, s->ranges, tiles,
                                   stream, V),
                "tile ranges");
+    }
+    if (s->st.tile_split == 0 && s->view_done.empty() && tiles > 0) {
+        // the blends launch the tiles longest pair list first (both passes use the order)
+        StageTimer tm(ctx, CS_STAGE_TILE_SORT, stream);
+        uint32_t *ctr = nullptr;
+        cudaError_t e = pool_alloc(ctx, (void **)&ctr, 2 * TILE_ORDER_CLASSES * 4, stream);
+        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&s->tile_order, (size_t)tiles * 4, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 2 * TILE_ORDER_CLASSES * 4, stream);
+        if (e == cudaSuccess) e = launch_tile_order(s->ranges, tiles, ctr, s->tile_order, stream);
+        pool_free(ctr, stream);
+        CS_TRY(e, "tile order");
     }
     if (s->st.tile_split > 0 && P > 0) {
         // tile split: which tiles are heavy, their chunk slots, the work items; the totals size the

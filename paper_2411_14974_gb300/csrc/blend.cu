@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
     __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
     uint32_t g, chunk = 0, slot = NO_SLOT;
     if (MODE == MODE_PLAIN) {
-        g = a.tile_offset + blockIdx.x;
+        g = a.tile_order ? a.tile_order[blockIdx.x] : a.tile_offset + blockIdx.x;
     } else {
         const uint2 it = (MODE == MODE_CHUNK ? a.split_items : a.split_heavy)[blockIdx.x];
         g = it.x;
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
     __shared__ uint32_t sidx_all[BWD_THREADS / 32][32];
     uint32_t g, chunk = 0, slot = NO_SLOT;
     if (MODE == MODE_PLAIN) {
-        g = a.tile_offset + blockIdx.x;
+        g = a.tile_order ? a.tile_order[blockIdx.x] : a.tile_offset + blockIdx.x;
     } else {  // a chunk of a heavy tile (see the tile split of the forward), or a whole light tile
         const uint2 it = a.split_items[blockIdx.x];
         g = it.x;
@@ -834,6 +834,38 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
     if (COUNT) flush_counts(counts, cnt);
 }
 
+// launch order: class of a tile = 31 - floor(log2(pairs + 1)), longest lists in the first class
+__device__ __forceinline__ uint32_t order_class(const uint2 &r) {
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    return (uint32_t)__clz(len + 1u);  // 31 for an empty tile, smaller for longer lists
+}
+
+__global__ void k_order_count(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *__restrict__ counters) {
+    __shared__ uint32_t hist[TILE_ORDER_CLASSES];
+    if (threadIdx.x < TILE_ORDER_CLASSES) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n_tiles) atomicAdd(&hist[order_class(ranges[g])], 1u);
+    __syncthreads();
+    if (threadIdx.x < TILE_ORDER_CLASSES && hist[threadIdx.x]) atomicAdd(&counters[threadIdx.x], hist[threadIdx.x]);
+}
+
+__global__ void k_order_place(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *__restrict__ counters,
+                              uint32_t *__restrict__ order) {
+    __shared__ uint32_t base[TILE_ORDER_CLASSES];
+    if (threadIdx.x < TILE_ORDER_CLASSES) {  // start of each class: the sizes of the classes before it
+        uint32_t b = 0;
+        for (int c = 0; c < (int)threadIdx.x; ++c) b += counters[c];
+        base[threadIdx.x] = b;
+    }
+    __syncthreads();
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tiles) return;
+    const uint32_t c = order_class(ranges[g]);
+    const uint32_t at = base[c] + atomicAdd(&counters[TILE_ORDER_CLASSES + c], 1u);
+    if (checked(at < n_tiles, CS_BAD_TILE)) order[at] = g;
+}
+
 // tile split planning: chunks of each heavy tile, 1 for each light tile
 __global__ void k_split_count(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t split,
                               uint32_t *__restrict__ heavy, uint32_t *__restrict__ light,
@@ -926,6 +958,15 @@ cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
     (void)s;
     return cudaSuccess;
 #endif
+}
+
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *counters, uint32_t *order,
+                              cudaStream_t s) {
+    if (n_tiles == 0) return cudaSuccess;
+    k_order_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, counters);
+    k_order_place<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, counters, order);
+    count_launches(2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_split_count(const uint2 *ranges, uint32_t n_tiles, uint32_t split, uint32_t *heavy, uint32_t *light,

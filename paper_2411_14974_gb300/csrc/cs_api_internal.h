@@ -53,6 +53,7 @@ struct cs_fwd_state {
     std::vector<cudaEvent_t> view_done;
     // tile split (settings.tile_split > 0): work items, heavy tiles, slots and chunk states, kept
     // for the backward
+    uint32_t *tile_order = nullptr;  // blend launch order of the tiles (longest lists first)
     uint2 *split_items = nullptr, *split_heavy = nullptr;
     uint32_t *split_slot = nullptr;
     float *chunk_state = nullptr;
