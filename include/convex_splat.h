@@ -196,7 +196,11 @@ typedef enum {
     CS_ARR_TILE_RANGES = 6,  /* uint32 [tiles][2]: [start, end) of each tile in the pair list; tiles of
                                 all views in view order, row major within a view */
     CS_ARR_N_LAST = 7,       /* uint32 [V][H][W]: 1 + pair index of the last contributor, 0 if none */
-    CS_ARR_HULLS = 8         /* uint32 [R]: hull size T in bits 0-3, vertex i in bits 4+3i.. */
+    CS_ARR_HULLS = 8,        /* uint32 [R]: hull size T in bits 0-3, vertex i in bits 4+3i.. */
+    CS_ARR_TILE_ORDER = 9    /* uint32 [tiles]: the order in which the blend kernels take the tiles, a
+                                permutation of the tile indices by decreasing floor(log2(pairs + 1))
+                                (any order within a class); empty (0 bytes) when the blends run in
+                                chunks (tile_split) or per view (serving) */
 } cs_array;
 cs_status cs_state_copy(const cs_fwd_state *state, int32_t which, void *host_dst, size_t capacity,
                         size_t *bytes_out);

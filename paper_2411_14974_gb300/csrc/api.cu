@@ -524,13 +524,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     if (s->st.tile_split == 0 && s->view_done.empty() && tiles > 0) {
         // the blends launch the tiles longest pair list first (both passes use the order)
         StageTimer tm(ctx, CS_STAGE_TILE_SORT, stream);
-        uint32_t *ctr = nullptr;
-        cudaError_t e = pool_alloc(ctx, (void **)&ctr, 2 * TILE_ORDER_CLASSES * 4, stream);
-        if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&s->tile_order, (size_t)tiles * 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 2 * TILE_ORDER_CLASSES * 4, stream);
-        if (e == cudaSuccess) e = launch_tile_order(s->ranges, tiles, ctr, s->tile_order, stream);
-        pool_free(ctr, stream);
-        CS_TRY(e, "tile order");
+        CS_TRY(pool_alloc(ctx, (void **)&s->tile_order, (size_t)tiles * 4, stream), "alloc");
+        CS_TRY(launch_tile_order(s->ranges, tiles, s->tile_order, stream), "tile order");
     }
     if (s->st.tile_split > 0 && P > 0) {
         // tile split: which tiles are heavy, their chunk slots, the work items; the totals size the
@@ -782,6 +777,7 @@ extern "C" cs_status cs_state_copy(const cs_fwd_state *s, int32_t which, void *h
         case CS_ARR_TILE_RANGES: src = s->ranges; bytes = (size_t)s->n_tiles * 8; break;
         case CS_ARR_N_LAST: src = s->n_last; bytes = pix * 4; break;
         case CS_ARR_HULLS: break;
+        case CS_ARR_TILE_ORDER: src = s->tile_order; bytes = s->tile_order ? (size_t)s->n_tiles * 4 : 0; break;
         default: return fail(CS_ERR_ARG, "unknown array %d", which);
     }
     if (which == CS_ARR_HULLS) bytes = (size_t)s->n_records * 4;

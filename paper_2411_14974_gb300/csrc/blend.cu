@@ -177,7 +177,7 @@ __device__ __forceinline__ bool stage_record(float4 *buf, int lane, int nh, uint
 // vector loads (as many as the record's hull lines need) and writes the staged form to dst, for
 // the same pixel blocks and with the same values as stage_record.  (Staging through the warp's
 // cp.async copies, as the forward does, costs this kernel register spills at its occupancy of
-// 7 CTAs per SM and was measured slower.)  Returns the same pre-test result.
+// 6 CTAs per SM and was measured slower.)  Returns the same pre-test result.
 template <int ROWS, int K>
 __device__ __forceinline__ bool stage_record_ldg(float4 *dst, const float4 *__restrict__ records, uint32_t r, float ox,
                                              float oy, const Settings &st) {
@@ -230,6 +230,24 @@ __device__ __forceinline__ bool stage_record_ldg(float4 *dst, const float4 *__re
     return pass;
 }
 
+// Packed FP32 (add / sub / mul / fma .f32x2): one instruction does the arithmetic of two independent
+// evaluations held in the two halves of a 64-bit register pair (the forward's two records of a
+// pixel, the backward's two pixels of a lane), rounding each half exactly like the scalar
+// instruction.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
 // Terms of one (pixel, convex) pair kept for the backward.
 struct PairTerms {
     float alpha, I, z, oI, phi2, S;
@@ -270,6 +288,43 @@ __device__ __forceinline__ int eval_pair(const float4 *__restrict__ rec, float l
 
 // work counters of the instrumented kernel variants: pairs visited, their hull lines, pairs past
 // the line pre-test, their hull lines, contributing pairs, pixels
+// eval_pair<0, NT> of two records for the same pixel at once, record 1 in the .x halves and record
+// 2 in the .y halves of the packed arithmetic, with the same values and codes as two calls of
+// eval_pair (two = false: record 2 is not evaluated and its code is 0).
+template <int NT>
+__device__ __forceinline__ void eval_two(const float4 *__restrict__ rec1, const float4 *__restrict__ rec2, bool two,
+                                         float lx, float ly, const Settings &st, int &code1, int &code2,
+                                         float2 &alpha) {
+    const float4 h1 = rec1[0], h2 = rec2[0];
+    float s1[NT], s2[NT];
+    float m1 = -__int_as_float(0x7f800000), m2 = m1;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const float4 L1 = rec1[3 + t], L2 = rec2[3 + t];
+        s1[t] = fmaf(L1.x, lx, fmaf(L1.y, ly, L1.z));
+        s2[t] = fmaf(L2.x, lx, fmaf(L2.y, ly, L2.z));
+        m1 = fmaxf(m1, s1[t]);
+        m2 = fmaxf(m2, s2[t]);
+    }
+    const bool act1 = !(m1 > h1.y), act2 = two && !(m2 > h2.y);
+    code1 = code2 = 0;
+    if (!(act1 || act2)) return;
+    const float2 M = make_float2(m1, m2);
+    float2 S = f2(0.f);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const float2 d = sub2(make_float2(s1[t], s2[t]), M);
+        S = add2(S, make_float2(ex2(d.x), ex2(d.y)));
+    }
+    const float2 phi2 = add2(M, make_float2(lg2(S.x), lg2(S.y)));
+    const float2 zx = mul2(make_float2(h1.x, h2.x), phi2);
+    const float2 zp = add2(f2(1.0f), make_float2(ex2(zx.x), ex2(zx.y)));
+    const float2 oI = mul2(make_float2(h1.z, h2.z), make_float2(rcp(zp.x), rcp(zp.y)));
+    alpha = make_float2(fminf(st.alpha_max, oI.x), fminf(st.alpha_max, oI.y));
+    if (act1) code1 = alpha.x >= st.tau ? 2 : 1;
+    if (act2) code2 = alpha.y >= st.tau ? 2 : 1;
+}
+
 constexpr int NCOUNT = 6;
 __device__ __forceinline__ void flush_counts(unsigned long long *dst, const unsigned long long (&c)[NCOUNT]) {
 #pragma unroll
@@ -391,20 +446,20 @@ __device__ __forceinline__ void walk_forward(const BlendArgs &a, uint32_t lo, ui
                 const bool two = bits != 0;
                 bits &= bits - 1;
                 const float4 *rec1 = wrec + j1 * SREC<K>, *rec2 = wrec + j2 * SREC<K>;
-                PairTerms p1, p2;
-                const int code1 = eval_pair<0, K>(rec1, lx, ly, st, p1);
-                const int code2 = two ? eval_pair<0, K>(rec2, lx, ly, st, p2) : 0;
+                int code1, code2;
+                float2 al;
+                eval_two<K>(rec1, rec2, two, lx, ly, st, code1, code2, al);
                 if (COUNT) {
                     count_pair(cnt, rec1, code1);
                     if (two) count_pair(cnt, rec2, code2);
                 }
                 if (code1 == 2) {
                     const float4 c = rec1[1];
-                    const float wgt = p1.alpha * q.T;
+                    const float wgt = al.x * q.T;
                     q.C0 = fmaf(wgt, c.x, q.C0);
                     q.C1 = fmaf(wgt, c.y, q.C1);
                     q.C2 = fmaf(wgt, c.z, q.C2);
-                    q.T = q.T * (1.0f - p1.alpha);
+                    q.T = q.T * (1.0f - al.x);
                     q.last = sidx[j1] + 1;
                     if (q.T < st.t_min) {
                         q.done = true;
@@ -413,11 +468,11 @@ __device__ __forceinline__ void walk_forward(const BlendArgs &a, uint32_t lo, ui
                 }
                 if (code2 == 2) {
                     const float4 c = rec2[1];
-                    const float wgt = p2.alpha * q.T;
+                    const float wgt = al.y * q.T;
                     q.C0 = fmaf(wgt, c.x, q.C0);
                     q.C1 = fmaf(wgt, c.y, q.C1);
                     q.C2 = fmaf(wgt, c.z, q.C2);
-                    q.T = q.T * (1.0f - p2.alpha);
+                    q.T = q.T * (1.0f - al.y);
                     q.last = sidx[j2] + 1;
                     if (q.T < st.t_min) {
                         q.done = true;
@@ -573,32 +628,12 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, u
 }
 
 // per-lane state of the backward's two pixels (rows r and r + 4 of the warp's 8x8 block)
-struct BwdPixels {
-    float Tc[2];               // transmittance behind the pair being undone
-    float G0[2], G1[2], G2[2];  // dL/dC
-    float GS[2];               // dL/dC . (colour seen behind the current pair, times T)
-    uint32_t last[2];          // pairs at or beyond this index did not contribute
+struct BwdPixels {           // .x: the lane's upper pixel, .y: its lower pixel (4 rows down)
+    float2 Tc;               // transmittance behind the pair being undone
+    float2 G0, G1, G2;       // dL/dC
+    float2 GS;               // dL/dC . (colour seen behind the current pair, times T)
+    uint32_t last[2];        // pairs at or beyond this index did not contribute
 };
-
-// The rest of eval_pair once the line values s[] of one pixel are known.
-template <int NT>
-__device__ __forceinline__ int eval_from_lines(const float (&s)[NT], float m, const float4 &h0, const Settings &st,
-                                               PairTerms &p) {
-    if (m > h0.y) return 0;
-    float S = 0.f;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        p.e[t] = ex2(s[t] - m);
-        S += p.e[t];
-    }
-    p.S = S;
-    p.phi2 = m + lg2(S);
-    p.z = ex2(h0.x * p.phi2);
-    p.I = rcp(1.0f + p.z);
-    p.oI = h0.z * p.I;
-    p.alpha = fminf(st.alpha_max, p.oI);
-    return p.alpha >= st.tau ? 2 : 1;
-}
 
 // Per-pair gradient words of a lane, packed: 3t + 0 = sum g_t x, 3t + 1 = sum g_t y, 3t + 2 = sum
 // g_t over the lane's two pixels (8x8-block coordinates), then dsigma', dopacity, dcolour (3); the
@@ -613,74 +648,95 @@ struct PackedWords {
 
 // Undoes record rec (pair index idx, NT lines) for both pixels of the lane: recovers T in front
 // of the pair, writes the lane's packed gradient words into v, and returns whether any of the two
-// pixels received a contribution.
+// pixels received a contribution.  Per pixel, the operations and their rounding are those of the
+// forward's evaluation (eval_pair), so alpha and T agree with the forward bit for bit.
 template <int NT, bool COUNT>
-__device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint32_t idx, float lx, float ly,
-                                           const Settings &st, BwdPixels &q, float (&v)[PackedWords<NT>::N],
-                                           unsigned long long (&cnt)[NCOUNT]) {
+__device__ __forceinline__ bool bwd_record(const float4 *__restrict__ rec, uint32_t idx, float2 LX, float2 LY,
+                                           float lx, float ly, const Settings &st, BwdPixels &q,
+                                           float (&v)[PackedWords<NT>::N], unsigned long long (&cnt)[NCOUNT]) {
     using PW = PackedWords<NT>;
     const float4 h0 = rec[0];
-    bool any_on = false;
-    float gt[2][NT];  // dphi2 e_t of each pixel (0 where the pixel adds no line gradient)
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-        for (int t = 0; t < NT; ++t) gt[k][t] = 0.f;
-#pragma unroll
-    for (int w = PW::SIG; w < PW::N; ++w) v[w] = 0.f;
-    // line values of both pixels from one read of each staged line (the lower pixel's block origin
-    // is the record's second C)
-    float sv[2][NT];
-    float mv[2] = {-__int_as_float(0x7f800000), -__int_as_float(0x7f800000)};
+    for (int w = 0; w < PW::N; ++w) v[w] = 0.f;
+    // line values of both pixels (the lower pixel's block origin is the record's second C)
+    float2 s[NT];
+    float m0 = -__int_as_float(0x7f800000), m1 = m0;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
         const float4 L = rec[3 + t];
-        sv[0][t] = fmaf(L.x, lx, fmaf(L.y, ly, L.z));
-        sv[1][t] = fmaf(L.x, lx, fmaf(L.y, ly, L.w));
-        mv[0] = fmaxf(mv[0], sv[0][t]);
-        mv[1] = fmaxf(mv[1], sv[1][t]);
+        s[t] = fma2(f2(L.x), LX, fma2(f2(L.y), LY, make_float2(L.z, L.w)));
+        m0 = fmaxf(m0, s[t].x);
+        m1 = fmaxf(m1, s[t].y);
     }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (idx >= q.last[k]) continue;
-        PairTerms p;
-        const int code = eval_from_lines<NT>(sv[k], mv[k], h0, st, p);
-        if (COUNT) count_pair(cnt, rec, code);
-        if (code != 2) continue;
-        any_on = true;
-        const float4 c = rec[1];
-        const float om = 1.0f - p.alpha;
-        const float inv = rcp(om);  // om >= 1 - alpha_max > 0
-        const float Tn = q.Tc[k] * inv;  // transmittance in front of this pair
-        // dC/dalpha = T_n c - S / (1 - alpha), S the colour behind: only dL/dC . S is needed
-        const float Gc = fmaf(q.G2[k], c.z, fmaf(q.G1[k], c.y, q.G0[k] * c.x));
-        const float dalpha = fmaf(Tn, Gc, -q.GS[k] * inv);
-        const float ta = Tn * p.alpha;
-        v[PW::RGB] += q.G0[k] * ta;
-        v[PW::RGB + 1] += q.G1[k] * ta;
-        v[PW::RGB + 2] += q.G2[k] * ta;
-        q.GS[k] = fmaf(ta, Gc, q.GS[k]);
-        q.Tc[k] = Tn;
-        if (p.oI < st.alpha_max) {
-            v[PW::OPA] += dalpha * p.I;
-            const float dI = dalpha * h0.z;
-            // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
-            const float dx = -dI * LN2 * p.z * p.I * p.I;
-            v[PW::SIG] += dx * p.phi2;
-            const float dphi2 = dx * h0.x * rcp(p.S);
-#pragma unroll
-            for (int t = 0; t < NT; ++t) gt[k][t] = dphi2 * p.e[t];
+    const bool act0 = idx < q.last[0] && !(m0 > h0.y), act1 = idx < q.last[1] && !(m1 > h0.y);
+    if (!(act0 || act1)) {
+        if (COUNT) {
+            if (idx < q.last[0]) count_pair(cnt, rec, 0);
+            if (idx < q.last[1]) count_pair(cnt, rec, 0);
         }
+        return false;
     }
+    const float2 M = make_float2(m0, m1);
+    float2 S = f2(0.f), e[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const float2 d = sub2(s[t], M);
+        e[t] = make_float2(ex2(d.x), ex2(d.y));
+        S = add2(S, e[t]);
+    }
+    const float2 phi2 = add2(M, make_float2(lg2(S.x), lg2(S.y)));
+    const float2 zx = mul2(f2(h0.x), phi2);
+    const float2 z = make_float2(ex2(zx.x), ex2(zx.y));
+    const float2 zp = add2(f2(1.0f), z);
+    const float2 I = make_float2(rcp(zp.x), rcp(zp.y));
+    const float2 oI = mul2(f2(h0.z), I);
+    const float2 alpha = make_float2(fminf(st.alpha_max, oI.x), fminf(st.alpha_max, oI.y));
+    const bool on0 = act0 && alpha.x >= st.tau, on1 = act1 && alpha.y >= st.tau;
+    if (COUNT) {
+        if (idx < q.last[0]) count_pair(cnt, rec, act0 ? (on0 ? 2 : 1) : 0);
+        if (idx < q.last[1]) count_pair(cnt, rec, act1 ? (on1 ? 2 : 1) : 0);
+    }
+    if (!(on0 || on1)) return false;
+    // both pixels are undone together; a pixel the pair does not reach keeps its state and adds
+    // zeros (selected, never multiplied, so an infinite z there cannot leak a NaN)
+    const float4 c = rec[1];
+    const float2 om = sub2(f2(1.0f), alpha);  // 1 - alpha >= 1 - alpha_max > 0
+    const float2 inv = make_float2(rcp(om.x), rcp(om.y));
+    const float2 Tn = mul2(q.Tc, inv);  // transmittance in front of this pair
+    // dC/dalpha = T_n c - S / (1 - alpha), S the colour behind: only dL/dC . S is needed
+    const float2 Gc = fma2(q.G2, f2(c.z), fma2(q.G1, f2(c.y), mul2(q.G0, f2(c.x))));
+    const float2 GSi = mul2(q.GS, inv);
+    const float2 dalpha = fma2(Tn, Gc, make_float2(-GSi.x, -GSi.y));
+    const float2 ta0 = mul2(Tn, alpha);
+    const float2 ta = make_float2(on0 ? ta0.x : 0.f, on1 ? ta0.y : 0.f);
+    const float2 pr = mul2(q.G0, ta), pg = mul2(q.G1, ta), pb = mul2(q.G2, ta);
+    v[PW::RGB] = pr.x + pr.y;
+    v[PW::RGB + 1] = pg.x + pg.y;
+    v[PW::RGB + 2] = pb.x + pb.y;
+    q.GS = fma2(ta, Gc, q.GS);
+    q.Tc = make_float2(on0 ? Tn.x : q.Tc.x, on1 ? Tn.y : q.Tc.y);
+    // alpha below the cap: opacity, sigma and line gradients
+    const bool g0 = on0 && oI.x < st.alpha_max, g1 = on1 && oI.y < st.alpha_max;
+    const float2 da = make_float2(g0 ? dalpha.x : 0.f, g1 ? dalpha.y : 0.f);
+    const float2 po = mul2(da, I);
+    v[PW::OPA] = po.x + po.y;
+    const float2 dI = mul2(da, f2(h0.z));
+    // I = 1/(1 + 2^x), dI/dx = -ln2 I (1 - I) = -ln2 z I^2
+    const float2 dx0 = mul2(mul2(mul2(mul2(make_float2(-dI.x, -dI.y), f2(LN2)), z), I), I);
+    const float2 dx = make_float2(g0 ? dx0.x : 0.f, g1 ? dx0.y : 0.f);
+    const float2 ps = mul2(dx, phi2);
+    v[PW::SIG] = ps.x + ps.y;
+    const float2 dphi2 = mul2(mul2(dx, f2(h0.x)), make_float2(rcp(S.x), rcp(S.y)));
     // the two pixels share x; the lower one's y is 4 more
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-        const float gs = gt[0][t] + gt[1][t];
+        const float2 gt = mul2(dphi2, e[t]);
+        const float gs = gt.x + gt.y;
         v[3 * t] = gs * lx;
-        v[3 * t + 1] = fmaf(gs, ly, 4.0f * gt[1][t]);
+        v[3 * t + 1] = fmaf(gs, ly, 4.0f * gt.y);
         v[3 * t + 2] = gs;
     }
-    return any_on;
+    return true;
 }
 
 // Reduce-scatter of N = 8, 16 or 32 values over the warp: returns, in lane l, the warp sum of
@@ -722,7 +778,7 @@ __device__ __forceinline__ float reduce_words(float (&v)[N], int lane) {
 }
 
 template <bool COUNT, int K, int MODE>
-__global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
+__global__ void __launch_bounds__(BWD_THREADS, 6) k_blend_backward(BlendArgs a, const float *__restrict__ dL_dimage,
                                                                 int64_t image_stride, float4 *__restrict__ grads,
                                                                 unsigned long long *counts) {
     __shared__ float4 srec[BWD_THREADS / 32][STAGE_F4<K>];
@@ -757,6 +813,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
 
     // pixel k of this lane is row (lane >> 3) of the upper (k = 0) or lower (k = 1) 8x4 half
     BwdPixels q;
+    float Tc[2], G0[2], G1[2], G2[2], GS[2];
     unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, 0};
     const size_t hw = (size_t)vd.width * vd.height;
     const float *dl = dL_dimage + v * image_stride;
@@ -764,33 +821,38 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const int py = by + (lane >> 3) + 4 * k;
-        q.Tc[k] = 1.0f;
-        q.G0[k] = q.G1[k] = q.G2[k] = 0.f;
+        Tc[k] = 1.0f;
+        G0[k] = G1[k] = G2[k] = 0.f;
         q.last[k] = 0;
         if (px < vd.width && py < vd.height) {
             const size_t pix = (size_t)py * vd.width + px;
-            q.G0[k] = dl[pix];
-            q.G1[k] = dl[hw + pix];
-            q.G2[k] = dl[2 * hw + pix];
-            q.Tc[k] = vd.t_final[pix];
+            G0[k] = dl[pix];
+            G1[k] = dl[hw + pix];
+            G2[k] = dl[2 * hw + pix];
+            Tc[k] = vd.t_final[pix];
             q.last[k] = vd.n_last[pix];
             cnt[5]++;
         }
         // colour seen behind the current pair (T_after times its colour, summed from the back),
         // kept as its product with dL/dC; it starts with the background
-        q.GS[k] = q.Tc[k] * fmaf(q.G2[k], st.bg[2], fmaf(q.G1[k], st.bg[1], q.G0[k] * st.bg[0]));
+        GS[k] = Tc[k] * fmaf(G2[k], st.bg[2], fmaf(G1[k], st.bg[1], G0[k] * st.bg[0]));
         if (MODE == MODE_CHUNK && slot != NO_SLOT) {
             // a chunk of a heavy tile starts from the transmittance after it and the colour behind
             // it, left by the forward's merge; its walk covers its own pairs only
             const int spx = split_pixel(bx - tx * TILE + (lane & 7), by - ty * TILE + (lane >> 3) + 4 * k);
-            q.Tc[k] = *state_word(a, slot + chunk, 3, spx);
-            q.GS[k] = fmaf(q.G2[k], *state_word(a, slot + chunk, 2, spx),
-                           fmaf(q.G1[k], *state_word(a, slot + chunk, 1, spx),
-                                q.G0[k] * *state_word(a, slot + chunk, 0, spx)));
+            Tc[k] = *state_word(a, slot + chunk, 3, spx);
+            GS[k] = fmaf(G2[k], *state_word(a, slot + chunk, 2, spx),
+                         fmaf(G1[k], *state_word(a, slot + chunk, 1, spx), G0[k] * *state_word(a, slot + chunk, 0, spx)));
             q.last[k] = min(q.last[k], range.y);
         }
         lmax = max(lmax, q.last[k]);
     }
+    q.Tc = make_float2(Tc[0], Tc[1]);
+    q.G0 = make_float2(G0[0], G0[1]);
+    q.G1 = make_float2(G1[0], G1[1]);
+    q.G2 = make_float2(G2[0], G2[1]);
+    q.GS = make_float2(GS[0], GS[1]);
+    const float2 LX = f2(lx), LY = f2(ly);
     const uint32_t wend = __reduce_max_sync(0xffffffffu, lmax);
     uint32_t pos = max(wend, range.x);
     while (pos > range.x) {
@@ -813,7 +875,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 7) k_blend_backward(BlendArgs a, 
             const uint32_t idx = sidx[j];
             using PW = PackedWords<K>;
             float v[PW::N];
-            const bool any_on = bwd_record<K, COUNT>(rec, idx, lx, ly, st, q, v, cnt);
+            const bool any_on = bwd_record<K, COUNT>(rec, idx, LX, LY, lx, ly, st, q, v, cnt);
             if (!__any_sync(0xffffffffu, any_on)) continue;
             // lane l < PW::USED: the warp sum of packed word l
             float word = reduce_words<PW::N>(v, lane);
@@ -840,30 +902,71 @@ __device__ __forceinline__ uint32_t order_class(const uint2 &r) {
     return (uint32_t)__clz(len + 1u);  // 31 for an empty tile, smaller for longer lists
 }
 
-__global__ void k_order_count(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *__restrict__ counters) {
-    __shared__ uint32_t hist[TILE_ORDER_CLASSES];
-    if (threadIdx.x < TILE_ORDER_CLASSES) hist[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < n_tiles) atomicAdd(&hist[order_class(ranges[g])], 1u);
-    __syncthreads();
-    if (threadIdx.x < TILE_ORDER_CLASSES && hist[threadIdx.x]) atomicAdd(&counters[threadIdx.x], hist[threadIdx.x]);
+// One CTA: a histogram of the classes, their exclusive scan, then each tile placed at the next free
+// slot of its class.  Lanes of a warp that share a class take their slots with one shared atomic.
+constexpr int ORDER_THREADS = 1024, ORDER_PER = 8;
+
+__device__ __forceinline__ uint32_t order_slot(uint32_t *counter, uint32_t c, bool active) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    const unsigned peers = __match_any_sync(act, c);
+    const int lead = __ffs(peers) - 1;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == lead) base = atomicAdd(&counter[c], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, lead);
+    return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void k_order_place(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t *__restrict__ counters,
-                              uint32_t *__restrict__ order) {
-    __shared__ uint32_t base[TILE_ORDER_CLASSES];
-    if (threadIdx.x < TILE_ORDER_CLASSES) {  // start of each class: the sizes of the classes before it
-        uint32_t b = 0;
-        for (int c = 0; c < (int)threadIdx.x; ++c) b += counters[c];
-        base[threadIdx.x] = b;
+__global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
+                                                            uint32_t *__restrict__ order) {
+    __shared__ uint32_t count[TILE_ORDER_CLASSES], next[TILE_ORDER_CLASSES];
+    if (threadIdx.x < TILE_ORDER_CLASSES) count[threadIdx.x] = 0;
+    __syncthreads();
+    // ORDER_PER tiles per thread per round, their ranges loaded together (one load latency a round);
+    // the bounds are the same for every lane of a warp, so the warp-wide votes see all 32 lanes
+    const uint32_t stride = ORDER_THREADS * ORDER_PER;
+    for (uint32_t base = 0; base < n_tiles; base += stride) {
+        uint32_t c[ORDER_PER];
+#pragma unroll
+        for (int j = 0; j < ORDER_PER; ++j) {
+            const uint32_t g = base + j * ORDER_THREADS + threadIdx.x;
+            c[j] = g < n_tiles ? order_class(ranges[g]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < ORDER_PER; ++j) {
+            const uint32_t g0 = base + j * ORDER_THREADS + (threadIdx.x & ~31u);
+            if (g0 < n_tiles) order_slot(count, c[j], g0 + (threadIdx.x & 31u) < n_tiles);
+        }
     }
     __syncthreads();
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_tiles) return;
-    const uint32_t c = order_class(ranges[g]);
-    const uint32_t at = base[c] + atomicAdd(&counters[TILE_ORDER_CLASSES + c], 1u);
-    if (checked(at < n_tiles, CS_BAD_TILE)) order[at] = g;
+    if (threadIdx.x < 32) {  // exclusive scan of the 32 class sizes
+        const uint32_t v = count[threadIdx.x];
+        uint32_t x = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if ((int)threadIdx.x >= d) x += y;
+        }
+        next[threadIdx.x] = x - v;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < n_tiles; base += stride) {
+        uint32_t c[ORDER_PER];
+#pragma unroll
+        for (int j = 0; j < ORDER_PER; ++j) {
+            const uint32_t g = base + j * ORDER_THREADS + threadIdx.x;
+            c[j] = g < n_tiles ? order_class(ranges[g]) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < ORDER_PER; ++j) {
+            const uint32_t g0 = base + j * ORDER_THREADS + (threadIdx.x & ~31u);
+            const uint32_t g = g0 + (threadIdx.x & 31u);
+            if (g0 < n_tiles) {
+                const uint32_t at = order_slot(next, c[j], g < n_tiles);
+                if (g < n_tiles && checked(at < n_tiles, CS_BAD_TILE)) order[at] = g;
+            }
+        }
+    }
 }
 
 // tile split planning: chunks of each heavy tile, 1 for each light tile
@@ -960,12 +1063,10 @@ cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
 #endif
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *counters, uint32_t *order,
-                              cudaStream_t s) {
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    k_order_count<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, counters);
-    k_order_place<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, counters, order);
-    count_launches(2);
+    k_tile_order<<<1, ORDER_THREADS, 0, s>>>(ranges, n_tiles, order);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -195,12 +195,10 @@ cudaError_t launch_split_items(const uint2 *ranges, uint32_t n_tiles, uint32_t s
                                unsigned int *heavy_fill, uint32_t *slot_of_tile, cudaStream_t s);
 constexpr int SPLIT_STATE_FLOATS = 5 * 256;  // per chunk slot: 5 words for each pixel of a 16x16 tile
 // Launch order of the blend CTAs: the tiles by decreasing floor(log2(pairs + 1)) (order within a
-// class free), so that the longest pair lists start first and do not trail the grid.  counters:
-// 2 x TILE_ORDER_CLASSES words, zeroed by the caller.  Each tile's outputs do not depend on when
-// its CTA runs.
+// class free), so that the longest pair lists start first and do not trail the grid.  One launch
+// of one CTA; order: n_tiles words.  Each tile's outputs do not depend on when its CTA runs.
 constexpr int TILE_ORDER_CLASSES = 32;
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *counters, uint32_t *order,
-                              cudaStream_t s);
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, cudaStream_t s);
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,

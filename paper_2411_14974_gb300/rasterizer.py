@@ -17,10 +17,10 @@ import torch
 from . import _binding as B
 
 ARRAYS = dict(records=0, depth_keys=1, rects=2, counts=3, pair_keys=4, pair_values=5, tile_ranges=6,
-              n_last=7, hulls=8)
+              n_last=7, hulls=8, tile_order=9)
 _ARRAY_DTYPES = dict(records=np.float32, depth_keys=np.uint32, rects=np.uint32, counts=np.uint32,
                      pair_keys=np.uint32, pair_values=np.uint32, tile_ranges=np.uint32, n_last=np.uint32,
-                     hulls=np.uint32)
+                     hulls=np.uint32, tile_order=np.uint32)
 
 
 @dataclasses.dataclass

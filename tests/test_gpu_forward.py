@@ -76,6 +76,16 @@ def check_pairs(state, discs, cams):
         want[gidx, 0] = starts
         want[gidx, 1] = ends
     assert (rng == want).all(), "tile ranges differ"
+    check_tile_order(state, want)
+
+
+def check_tile_order(state, ranges):
+    """The blend launch order: every tile exactly once, by decreasing floor(log2(pairs + 1))."""
+    order = state.array("tile_order").astype(np.int64)
+    assert len(order) == len(ranges)
+    assert (np.sort(order) == np.arange(len(ranges))).all(), "tile order is not a permutation"
+    cls = np.floor(np.log2(ranges[order, 1] - ranges[order, 0] + 1.0))
+    assert (np.diff(cls) <= 0).all(), "tile order is not longest class first"
 
 
 def check_image(img, ref, ill, max_ill=0.02):
