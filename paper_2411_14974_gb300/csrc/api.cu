@@ -389,7 +389,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     CS_TRY(pool_alloc(ctx, (void **)&s->rects, (size_t)R * 8, stream), "alloc rects");
     CS_TRY(pool_alloc(ctx, (void **)&s->counts, (size_t)R * 4, stream), "alloc counts");
     CS_TRY(pool_alloc(ctx, (void **)&s->bboxes, (size_t)R * 16, stream), "alloc boxes");
-    CS_TRY(pool_alloc(ctx, (void **)&radii, (size_t)R * 4, stream), "alloc radii");
+    CS_TRY(pool_alloc(ctx, (void **)&radii, (size_t)R * 8, stream), "alloc radii");  // radii, kept masks
     CS_TRY(pool_alloc(ctx, (void **)&s->ranges, (size_t)tiles * 8, stream), "alloc ranges");
     CS_TRY(pool_alloc(ctx, (void **)&s->n_last, pix_total * 4, stream), "alloc n_last");
     {
@@ -414,7 +414,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     {
         StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
         PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes, radii,
-                         reinterpret_cast<PreprocessStats *>(total)};
+                         reinterpret_cast<uint32_t *>(radii + R), reinterpret_cast<PreprocessStats *>(total)};
         CS_TRY(launch_preprocess(s->views_dev, s->views.data(), V, max_n, s->k, s->st, po, stream), "preprocess");
     }
     {
@@ -494,7 +494,8 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         CS_TRY(pool_alloc(ctx, (void **)&s->pair_vals, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pk_b, P * 4, stream), "alloc pairs");
         CS_TRY(pool_alloc(ctx, (void **)&pv_b, P * 4, stream), "alloc pairs");
-        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii, s->bboxes,
+        CS_TRY(launch_emit_pairs(s->views_dev, V, sorted, offsets, s->counts, s->rects, s->records, radii,
+                                 reinterpret_cast<const uint32_t *>(radii + R), s->bboxes,
                                  R, local_bits, s->mask_shift, s->pair_keys, s->pair_vals, stream, (uint32_t)P),
                "emit pairs");
         pool_free(radii, stream);

@@ -77,6 +77,8 @@ struct PreprocessOut {
     uint32_t *counts;      // [R]
     float4 *bboxes;        // [R] pixel box (xmin, ymin, xmax, ymax) holding every pixel with alpha >= tau
     float *radii;          // [R] kappa r, the tile test's bound in record units
+    uint32_t *kept;        // [R] rectangles of at most 32 tiles: bit q set when tile q (row-major in
+                           // the rectangle) holds pairs of the record (after the exact tile test)
     PreprocessStats *stats;  // zeroed before the launch
 };
 cudaError_t launch_preprocess(const ViewDesc *views_dev, const ViewDesc *views_host, int n_views, int64_t max_n,
@@ -126,9 +128,10 @@ cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint3
 constexpr int BLOCK_MASK_BITS = 8;
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
-                              const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
-                              int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
-                              cudaStream_t s, uint32_t n_pairs = 0xffffffffu);
+                              const float4 *records, const float *radii, const uint32_t *kept,
+                              const float4 *bboxes, int64_t n_records, int local_bits, int mask_shift,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s,
+                              uint32_t n_pairs = 0xffffffffu);
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
                                int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s, int n_views);
 

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
     const int64_t rec = vd.rec_base + i;
     const float *P = sp + threadIdx.x * PS;
 
-    uint32_t depth_key = 0xffffffffu, count = 0;
+    uint32_t depth_key = 0xffffffffu, count = 0, kept = 0;
     uint2 rect = make_uint2(0, 0);
     bool drawn = false, coop = false;
     float w[REC_WORDS];
@@ -202,12 +202,18 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
         const float rk = __fmul_rn(rp, kappa);
         const uint32_t area = (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
         count = area;
+        kept = area <= 32u ? (area == 32u ? 0xffffffffu : (1u << area) - 1u) : 0u;
         if (st.tile_test && !full && area >= (uint32_t)SAT_MIN_TILES && area <= (uint32_t)SAT_MAX_TILES) {
             if (area <= (uint32_t)SAT_SERIAL_TILES) {
                 count = 0;
+                kept = 0;
+                uint32_t q = 0;
                 for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx)
-                        count += tile_kept(w + R_LINES, T, hu[0], hv[0], rk, tx, ty) ? 1u : 0u;
+                    for (int tx = tx0; tx <= tx1; ++tx, ++q)
+                        if (tile_kept(w + R_LINES, T, hu[0], hv[0], rk, tx, ty)) {
+                            ++count;
+                            kept |= 1u << q;
+                        }
                 if (count == 0) break;
             } else {
                 coop = true;  // counted by the whole warp below
@@ -242,13 +248,18 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
             const uint32_t x0 = rx & 0xffffu, y0 = ry & 0xffffu;
             const uint32_t wd = (rx >> 16) - x0 + 1, ar = wd * ((ry >> 16) - y0 + 1);
             const float ax = slot[3 * KMAX], ay = slot[3 * KMAX + 1], rk = slot[3 * KMAX + 2];
-            uint32_t kept = 0;
-            for (uint32_t q = (uint32_t)lane; q < ar; q += 32)
-                kept += tile_kept(slot, Ts, ax, ay, rk, (int)(x0 + q % wd), (int)(y0 + q / wd)) ? 1u : 0u;
-            kept = __reduce_add_sync(0xffffffffu, kept);
+            uint32_t n_kept = 0, first = 0;
+            for (uint32_t base = 0; base < ar; base += 32) {  // warp-uniform bounds
+                const uint32_t q = base + (uint32_t)lane;
+                const bool keep = q < ar && tile_kept(slot, Ts, ax, ay, rk, (int)(x0 + q % wd), (int)(y0 + q / wd));
+                const uint32_t b = __ballot_sync(0xffffffffu, keep);
+                if (base == 0) first = b;
+                n_kept += (uint32_t)__popc(b);
+            }
             if (lane == src) {
-                count = kept;
-                drawn = kept != 0;
+                count = n_kept;
+                drawn = n_kept != 0;
+                kept = ar <= 32u ? first : 0u;
             }
             __syncwarp();
         }
@@ -279,6 +290,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 6) k_preprocess(const ViewDesc *_
             srec[threadIdx.x * RS + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         out.bboxes[rec] = bbox;
         out.radii[rec] = radius;
+        out.kept[rec] = kept;
     }
     sdrawn[threadIdx.x] = drawn ? 1 : 0;
     if (i < n) {

@@ -351,19 +351,34 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &bb, uint32_t tx, ui
     return m;
 }
 
+// position of the set bit of m that has k set bits below it (k < popc(m))
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t k) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const uint32_t low = (uint32_t)__popc(m & ((1u << w) - 1u));
+        if (k >= low) {
+            k -= low;
+            m >>= w;
+            pos += (uint32_t)w;
+        }
+    }
+    return pos;
+}
+
 __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const uint32_t *__restrict__ sorted,
                        const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ counts,
                        const uint2 *__restrict__ rects, const float4 *__restrict__ records,
-                       const float *__restrict__ radii, const float4 *__restrict__ bboxes, int64_t n_records,
-                       int local_bits, int mask_shift, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                       uint32_t n_pairs) {
+                       const float *__restrict__ radii, const uint32_t *__restrict__ kept,
+                       const float4 *__restrict__ bboxes, int64_t n_records, int local_bits, int mask_shift,
+                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t n_pairs) {
     // the block mask of tile (tx, ty) for box bb, at its place in the key (0 without masks)
     auto mask_bits = [&](const float4 &bb, uint32_t tx, uint32_t ty) -> uint32_t {
         return mask_shift ? block_mask(bb, tx, ty) << mask_shift : 0u;
     };
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t r = 0, cnt = 0, area = 0, o = 0xffffffffu, hi = 0, tiles_x = 0;
+    uint32_t r = 0, cnt = 0, area = 0, o = 0xffffffffu, hi = 0, tiles_x = 0, km = 0;
     uint2 rc = make_uint2(0, 0);
     float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j < n_records) {
@@ -377,16 +392,19 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
             const int v = view_of_record(views, n_views, r);
             hi = (uint32_t)v << local_bits;
             tiles_x = (uint32_t)views[v].tiles_x;
+            if (cnt != area && area <= 32u) km = kept[r];
         }
     }
-    const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-    const bool full = cnt != 0 && cnt == area;  // every tile of the rectangle
-    const bool coop = cnt != 0 && cnt != area && area > (uint32_t)SAT_SERIAL_TILES;
-    if (__any_sync(0xffffffffu, full)) {
+    const bool full = cnt != 0 && cnt == area;                     // every tile of the rectangle
+    const bool masked = cnt != 0 && cnt != area && area <= 32u;     // the kept tiles of a small one
+    const bool coop = cnt != 0 && cnt != area && area > 32u;        // a large rectangle, tested here
+    if (__any_sync(0xffffffffu, full || masked)) {
         // The warp's records, consecutive in depth order, own the contiguous output range from
-        // lane 0's offset to the end of its last record; the full rectangles' pairs are written
-        // with consecutive addresses, output p belonging to the last lane whose offset is <= p
-        // (offsets do not decrease with the lane; lanes past the end hold 0xffffffff).
+        // lane 0's offset to the end of its last record; the pairs of full and masked rectangles
+        // are written with consecutive addresses, output p belonging to the last lane whose offset
+        // is <= p (offsets do not decrease with the lane; lanes past the end hold 0xffffffff).
+        // The k-th pair of a rectangle is its k-th tile in row-major order (full), or the tile of
+        // its k-th kept bit (masked), the order in which the preprocess counted them.
         const uint32_t wb = __shfl_sync(0xffffffffu, o, 0);
         const uint32_t we = __reduce_max_sync(0xffffffffu, j < n_records ? o + cnt : 0u);
         for (uint32_t p0 = wb; p0 < we; p0 += 32) {
@@ -395,42 +413,24 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1)
                 if (__shfl_sync(0xffffffffu, o, s + step) <= p) s += step;
-            const bool fs = __shfl_sync(0xffffffffu, full, s);
+            const bool fs = __shfl_sync(0xffffffffu, full, s), ms = __shfl_sync(0xffffffffu, masked, s);
             const uint32_t os = __shfl_sync(0xffffffffu, o, s), rs = __shfl_sync(0xffffffffu, r, s);
             const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, s), ry = __shfl_sync(0xffffffffu, rc.y, s);
             const uint32_t hs = __shfl_sync(0xffffffffu, hi, s), txs = __shfl_sync(0xffffffffu, tiles_x, s);
+            const uint32_t kms = __shfl_sync(0xffffffffu, km, s);
             float4 bs;
             bs.x = __shfl_sync(0xffffffffu, bb.x, s);
             bs.y = __shfl_sync(0xffffffffu, bb.y, s);
             bs.z = __shfl_sync(0xffffffffu, bb.z, s);
             bs.w = __shfl_sync(0xffffffffu, bb.w, s);
-            if (p < we && fs && checked(p < n_pairs, CS_BAD_PAIR_SLOT)) {
+            if (p < we && (fs || ms) && checked(p < n_pairs, CS_BAD_PAIR_SLOT)) {
                 const uint32_t k = p - os, wd = (rx >> 16) - (rx & 0xffffu) + 1;
-                const uint32_t ty = (ry & 0xffffu) + k / wd, tx = (rx & 0xffffu) + k % wd;
+                const uint32_t q = ms ? nth_set_bit(kms, k) : k;
+                const uint32_t ty = (ry & 0xffffu) + q / wd, tx = (rx & 0xffffu) + q % wd;
                 keys[p] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
                 vals[p] = rs;
             }
         }
-    }
-    if (cnt != 0 && !full && !coop) {  // small rectangle: the same exact test on the same record values
-        float w[REC_WORDS];
-        const float4 *rec = records + (size_t)r * (REC_WORDS / 4);
-#pragma unroll
-        for (int q = 0; q < REC_WORDS / 4; ++q) {
-            const float4 f = rec[q];
-            w[4 * q] = f.x; w[4 * q + 1] = f.y; w[4 * q + 2] = f.z; w[4 * q + 3] = f.w;
-        }
-        const int T = (int)hull_pack_count(__float_as_uint(w[R_HULL]));
-        const float rk = radii[r];
-        for (uint32_t ty = ty0; ty <= ty1; ++ty)
-            for (uint32_t tx = tx0; tx <= tx1; ++tx)
-                if (tile_kept(w + R_LINES, T, w[R_AX], w[R_AY], rk, (int)tx, (int)ty)) {
-                    if (checked(o < n_pairs, CS_BAD_PAIR_SLOT)) {
-                        keys[o] = mask_bits(bb, tx, ty) | hi | (ty * tiles_x + tx);
-                        vals[o] = r;
-                    }
-                    ++o;
-                }
     }
     uint32_t pending = __ballot_sync(0xffffffffu, coop);
     while (pending) {  // large rectangles: the warp tests 32 tiles at a time, kept ones in row-major order
@@ -474,17 +474,39 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
 }
 
 // [start, end) of every (view, tile) group of the sorted pairs, stored at the global tile index
+// RANGE_ITEMS consecutive sorted keys per thread (two 16-byte loads), each compared with its
+// neighbours; only the first and last pair of a (view, tile) group look up the view and write.
+constexpr int RANGE_ITEMS = 8;
 __global__ void k_ranges(const uint32_t *__restrict__ keys, int64_t n, const ViewDesc *__restrict__ views,
                          int local_bits, uint32_t key_mask, uint2 *__restrict__ ranges, int n_views,
                          int64_t n_tiles) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t k = keys[i] & key_mask;
-    if (!checked((int64_t)(k >> local_bits) < n_views, CS_BAD_TILE)) return;
-    const uint32_t g = views[k >> local_bits].tile_base + (k & ((1u << local_bits) - 1u));
-    if (!checked((int64_t)g < n_tiles, CS_BAD_TILE)) return;
-    if (i == 0 || (keys[i - 1] & key_mask) != k) ranges[g].x = (uint32_t)i;
-    if (i == n - 1 || (keys[i + 1] & key_mask) != k) ranges[g].y = (uint32_t)(i + 1);
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * RANGE_ITEMS;
+    if (i0 >= n) return;
+    uint32_t k[RANGE_ITEMS + 2];  // keys i0 - 1 .. i0 + RANGE_ITEMS (masked)
+    if (i0 + RANGE_ITEMS <= n && (reinterpret_cast<uintptr_t>(keys) & 15) == 0) {
+        const uint4 a = reinterpret_cast<const uint4 *>(keys + i0)[0], b = reinterpret_cast<const uint4 *>(keys + i0)[1];
+        k[1] = a.x; k[2] = a.y; k[3] = a.z; k[4] = a.w; k[5] = b.x; k[6] = b.y; k[7] = b.z; k[8] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < RANGE_ITEMS; ++q) k[q + 1] = i0 + q < n ? keys[i0 + q] : 0u;
+    }
+    k[0] = i0 > 0 ? keys[i0 - 1] : 0u;
+    k[RANGE_ITEMS + 1] = i0 + RANGE_ITEMS < n ? keys[i0 + RANGE_ITEMS] : 0u;
+#pragma unroll
+    for (int q = 0; q < RANGE_ITEMS + 2; ++q) k[q] &= key_mask;
+#pragma unroll
+    for (int q = 0; q < RANGE_ITEMS; ++q) {
+        const int64_t i = i0 + q;
+        if (i >= n) break;
+        const uint32_t kc = k[q + 1];
+        const bool start = i == 0 || k[q] != kc, end = i == n - 1 || k[q + 2] != kc;
+        if (!(start || end)) continue;
+        if (!checked((int64_t)(kc >> local_bits) < n_views, CS_BAD_TILE)) continue;
+        const uint32_t g = views[kc >> local_bits].tile_base + (kc & ((1u << local_bits) - 1u));
+        if (!checked((int64_t)g < n_tiles, CS_BAD_TILE)) continue;
+        if (start) ranges[g].x = (uint32_t)i;
+        if (end) ranges[g].y = (uint32_t)(i + 1);
+    }
 }
 
 }  // namespace
@@ -595,14 +617,14 @@ cudaError_t launch_view_keys(const ViewDesc *views_dev, int n_views, const uint3
 
 cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint32_t *sorted_records,
                               const uint32_t *offsets, const uint32_t *counts, const uint2 *rects,
-                              const float4 *records, const float *radii, const float4 *bboxes, int64_t n_records,
-                              int local_bits, int mask_shift, uint32_t *pair_keys, uint32_t *pair_vals,
-                              cudaStream_t s, uint32_t n_pairs) {
+                              const float4 *records, const float *radii, const uint32_t *kept,
+                              const float4 *bboxes, int64_t n_records, int local_bits, int mask_shift,
+                              uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s, uint32_t n_pairs) {
     if (n_records <= 0) return cudaSuccess;
     if (mask_shift < 0 || (mask_shift > 0 && mask_shift + BLOCK_MASK_BITS > 32)) return cudaErrorInvalidValue;
     k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
-                                                               rects, records, radii, bboxes, n_records, local_bits,
-                                                               mask_shift, pair_keys, pair_vals, n_pairs);
+                                                               rects, records, radii, kept, bboxes, n_records,
+                                                               local_bits, mask_shift, pair_keys, pair_vals, n_pairs);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -612,8 +634,9 @@ cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
     const uint32_t key_mask = mask_shift ? (1u << mask_shift) - 1u : 0xffffffffu;
-    k_ranges<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, key_mask,
-                                                              ranges, n_views, n_tiles);
+    const int64_t threads = (n_pairs + RANGE_ITEMS - 1) / RANGE_ITEMS;
+    k_ranges<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(pair_keys, n_pairs, views_dev, local_bits, key_mask,
+                                                               ranges, n_views, n_tiles);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -109,6 +109,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     uint32_t *counts = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     float4 *bboxes = c.take<float4>(CS_STATIC_MAX_CONVEXES);
     float *radii = c.take<float>(CS_STATIC_MAX_CONVEXES);
+    uint32_t *kept = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *ka = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *kb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *va = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES), *vb = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
     uint32_t *offsets = c.take<uint32_t>(CS_STATIC_MAX_CONVEXES);
@@ -127,7 +128,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     e = cudaMemcpyAsync(views_dev, &vd, sizeof vd, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(totals, 0, sizeof(PreprocessStats), stream);
     if (e == cudaSuccess) {
-        PreprocessOut po{records, depth_keys, rects, counts, bboxes, radii, totals};
+        PreprocessOut po{records, depth_keys, rects, counts, bboxes, radii, kept, totals};
         e = launch_preprocess(views_dev, &vd, 1, R, scene->k, s, po, stream);
     }
     // one host synchronisation: the pair count and the drawn records' depth-key range
@@ -151,7 +152,7 @@ extern "C" cs_status cs_forward_static(const cs_scene *scene, const cs_camera *c
     const int local_bits = bits_for(tiles);
     const int mask_shift = local_bits + BLOCK_MASK_BITS <= 32 ? local_bits : 0;
     if (e == cudaSuccess)
-        e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, bboxes, R, local_bits,
+        e = launch_emit_pairs(views_dev, 1, sorted, offsets, counts, rects, records, radii, kept, bboxes, R, local_bits,
                               mask_shift, pk, pv, stream, (uint32_t)P);
     if (e == cudaSuccess) e = radix_sort_pairs(pk, pv, pk2, pv2, (int64_t)P, local_bits, radix_tmp, scan_tmp, &in_b,
                                                stream);

@@ -107,10 +107,11 @@ def test_pair_keys_without_room_for_block_masks():
 
 def test_measured_alu_rates_are_plausible():
     """The per-SM rates used as roofline peaks: the transcendental unit and the FP32 FMA pipe,
-    measured with clock64 on the device, within a factor of two of 16 and 128 per clock."""
+    measured with clock64 on the device, within a factor of two of 16-32 and 128 per clock."""
     import paper_2411_14974_gb300 as cs
     r = cs.alu_rates(0)
-    assert 8.0 <= r["mufu_per_clk_sm"] <= 32.0, r
+    assert 8.0 <= r["mufu_per_clk_sm"] <= 64.0, r
     assert 64.0 <= r["fma_per_clk_sm"] <= 256.0, r
     assert 500.0 <= r["sm_mhz"] <= 3000.0, r
     assert r["sms"] >= 1
+
