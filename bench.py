@@ -641,7 +641,7 @@ def run_ours(args):
         n_conv = sc.n
         sh_w = 3 * (sc.sh_degree + 1) ** 2
         p_bytes = 4 * (sc.k * 3 + 3 + sh_w)
-        pre_bytes = n_conv * (p_bytes + 128 + 4 + 4 + 8 + 16 + 4)
+        pre_bytes = n_conv * (p_bytes + 128 + 4 + 4 + 8 + 16 + 4 + 4)
         # backward (the step writes the gradients, cs_backward_write): parameters, the record's first
         # 32 bytes (hull), the 128-byte gradient record, the points, SH, delta, sigma and opacity
         # gradients written

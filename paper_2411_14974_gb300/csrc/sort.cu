@@ -351,6 +351,8 @@ __device__ __forceinline__ uint32_t block_mask(const float4 &bb, uint32_t tx, ui
     return m;
 }
 
+constexpr int EMIT_THREADS = 256;  // records per emit block
+
 // position of the set bit of m that has k set bits below it (k < popc(m))
 __device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t k) {
     uint32_t pos = 0;
@@ -398,39 +400,46 @@ __global__ void k_emit(const ViewDesc *__restrict__ views, int n_views, const ui
     const bool full = cnt != 0 && cnt == area;                     // every tile of the rectangle
     const bool masked = cnt != 0 && cnt != area && area <= 32u;     // the kept tiles of a small one
     const bool coop = cnt != 0 && cnt != area && area > 32u;        // a large rectangle, tested here
-    if (__any_sync(0xffffffffu, full || masked)) {
-        // The warp's records, consecutive in depth order, own the contiguous output range from
-        // lane 0's offset to the end of its last record; the pairs of full and masked rectangles
-        // are written with consecutive addresses, output p belonging to the last lane whose offset
-        // is <= p (offsets do not decrease with the lane; lanes past the end hold 0xffffffff).
-        // The k-th pair of a rectangle is its k-th tile in row-major order (full), or the tile of
-        // its k-th kept bit (masked), the order in which the preprocess counted them.
-        const uint32_t wb = __shfl_sync(0xffffffffu, o, 0);
-        const uint32_t we = __reduce_max_sync(0xffffffffu, j < n_records ? o + cnt : 0u);
-        for (uint32_t p0 = wb; p0 < we; p0 += 32) {
-            const uint32_t p = p0 + (uint32_t)lane;
-            int s = 0;
+    // The block's records, consecutive in depth order, own the contiguous output range from its
+    // first offset to the end of its last record.  The pairs of full and masked rectangles are
+    // written by all threads of the block with consecutive addresses, output p belonging to the
+    // last record whose offset is <= p (offsets do not decrease; threads past the end hold
+    // 0xffffffff), so that a record with many tiles is spread over the block.  The k-th pair of a
+    // rectangle is its k-th tile in row-major order (full), or the tile of its k-th kept bit
+    // (masked), the order in which the preprocess counted them.
+    __shared__ uint32_t s_o[EMIT_THREADS], s_r[EMIT_THREADS], s_rx[EMIT_THREADS], s_ry[EMIT_THREADS];
+    __shared__ uint32_t s_hi[EMIT_THREADS], s_txs[EMIT_THREADS], s_km[EMIT_THREADS];
+    __shared__ uint8_t s_kind[EMIT_THREADS];
+    __shared__ float4 s_bb[EMIT_THREADS];
+    __shared__ uint32_t s_end[EMIT_THREADS / 32];
+    s_o[threadIdx.x] = o;
+    s_r[threadIdx.x] = r;
+    s_rx[threadIdx.x] = rc.x;
+    s_ry[threadIdx.x] = rc.y;
+    s_hi[threadIdx.x] = hi;
+    s_txs[threadIdx.x] = tiles_x;
+    s_km[threadIdx.x] = km;
+    s_kind[threadIdx.x] = full ? 1 : masked ? 2 : 0;
+    s_bb[threadIdx.x] = bb;
+    const uint32_t wend = __reduce_max_sync(0xffffffffu, j < n_records ? o + cnt : 0u);
+    if (lane == 0) s_end[threadIdx.x >> 5] = wend;
+    __syncthreads();
+    uint32_t be = 0;
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                if (__shfl_sync(0xffffffffu, o, s + step) <= p) s += step;
-            const bool fs = __shfl_sync(0xffffffffu, full, s), ms = __shfl_sync(0xffffffffu, masked, s);
-            const uint32_t os = __shfl_sync(0xffffffffu, o, s), rs = __shfl_sync(0xffffffffu, r, s);
-            const uint32_t rx = __shfl_sync(0xffffffffu, rc.x, s), ry = __shfl_sync(0xffffffffu, rc.y, s);
-            const uint32_t hs = __shfl_sync(0xffffffffu, hi, s), txs = __shfl_sync(0xffffffffu, tiles_x, s);
-            const uint32_t kms = __shfl_sync(0xffffffffu, km, s);
-            float4 bs;
-            bs.x = __shfl_sync(0xffffffffu, bb.x, s);
-            bs.y = __shfl_sync(0xffffffffu, bb.y, s);
-            bs.z = __shfl_sync(0xffffffffu, bb.z, s);
-            bs.w = __shfl_sync(0xffffffffu, bb.w, s);
-            if (p < we && (fs || ms) && checked(p < n_pairs, CS_BAD_PAIR_SLOT)) {
-                const uint32_t k = p - os, wd = (rx >> 16) - (rx & 0xffffu) + 1;
-                const uint32_t q = ms ? nth_set_bit(kms, k) : k;
-                const uint32_t ty = (ry & 0xffffu) + q / wd, tx = (rx & 0xffffu) + q % wd;
-                keys[p] = mask_bits(bs, tx, ty) | hs | (ty * txs + tx);
-                vals[p] = rs;
-            }
-        }
+    for (int q = 0; q < EMIT_THREADS / 32; ++q) be = max(be, s_end[q]);
+    for (uint32_t p = s_o[0] + threadIdx.x; p < be; p += EMIT_THREADS) {
+        int sr = 0;
+#pragma unroll
+        for (int step = EMIT_THREADS / 2; step >= 1; step >>= 1)
+            if (s_o[sr + step] <= p) sr += step;
+        const int kind = s_kind[sr];
+        if (kind == 0 || !checked(p < n_pairs, CS_BAD_PAIR_SLOT)) continue;
+        const uint32_t rx = s_rx[sr], ry = s_ry[sr];
+        const uint32_t k = p - s_o[sr], wd = (rx >> 16) - (rx & 0xffffu) + 1;
+        const uint32_t q = kind == 2 ? nth_set_bit(s_km[sr], k) : k;
+        const uint32_t ty = (ry & 0xffffu) + q / wd, tx = (rx & 0xffffu) + q % wd;
+        keys[p] = mask_bits(s_bb[sr], tx, ty) | s_hi[sr] | (ty * s_txs[sr] + tx);
+        vals[p] = s_r[sr];
     }
     uint32_t pending = __ballot_sync(0xffffffffu, coop);
     while (pending) {  // large rectangles: the warp tests 32 tiles at a time, kept ones in row-major order
@@ -622,9 +631,10 @@ cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint
                               uint32_t *pair_keys, uint32_t *pair_vals, cudaStream_t s, uint32_t n_pairs) {
     if (n_records <= 0) return cudaSuccess;
     if (mask_shift < 0 || (mask_shift > 0 && mask_shift + BLOCK_MASK_BITS > 32)) return cudaErrorInvalidValue;
-    k_emit<<<(unsigned)((n_records + 255) / 256), 256, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts,
-                                                               rects, records, radii, kept, bboxes, n_records,
-                                                               local_bits, mask_shift, pair_keys, pair_vals, n_pairs);
+    const unsigned blocks = (unsigned)((n_records + EMIT_THREADS - 1) / EMIT_THREADS);
+    k_emit<<<blocks, EMIT_THREADS, 0, s>>>(views_dev, n_views, sorted_records, offsets, counts, rects, records, radii,
+                                           kept, bboxes, n_records, local_bits, mask_shift, pair_keys, pair_vals,
+                                           n_pairs);
     count_launches(1);
     return cudaGetLastError();
 }
