@@ -9,4 +9,4 @@ from .rasterizer import (ARRAYS, PARAMS, WORK_FIELDS, Context, RefineSettings, S
                          alu_rates,
                          Settings, State, TrainConfig, Trainer, adam_step, backward, camera_struct, forward,
                          launch_count, loss_l1_dssim, profile_enable, profile_read, refine, render, step_host,
-                         work_counts)
+                         step_host_submit, step_host_wait, work_counts)

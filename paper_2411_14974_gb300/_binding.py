@@ -69,6 +69,10 @@ _PROTOTYPES = {
                                       ctypes.POINTER(ctypes.c_int64)]),
     "cs_step_host": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera), ctypes.c_int32,
                                     ctypes.POINTER(CsSettings), _P, _P, _P, _P, _P, _P, _P, _P]),
+    "cs_step_host_submit": (ctypes.c_int, [_P, ctypes.POINTER(CsScene), ctypes.POINTER(CsCamera),
+                                           ctypes.POINTER(CsSettings), _P, _P, _P, _P, _P, _P, _P,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "cs_step_host_wait": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "cs_profile_enable": (ctypes.c_int, [_P, ctypes.c_int32]),
     "cs_profile_read": (ctypes.c_int, [_P, _P, _P]),
     "cs_kernel_launch_count": (ctypes.c_uint64, []),

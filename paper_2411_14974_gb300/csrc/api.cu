@@ -177,6 +177,15 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
+    for (auto &sl : ctx->host_slots) {
+        if (sl.buf) cudaFree(sl.buf);
+        if (sl.uploaded) cudaEventDestroy(sl.uploaded);
+        if (sl.computed) cudaEventDestroy(sl.computed);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    if (ctx->upload_stream) cudaStreamDestroy(ctx->upload_stream);
+    if (ctx->compute_stream) cudaStreamDestroy(ctx->compute_stream);
+    if (ctx->download_stream) cudaStreamDestroy(ctx->download_stream);
     if (ctx->host_total) cudaFreeHost(ctx->host_total);
     if (ctx->totals_ready) cudaEventDestroy(ctx->totals_ready);
     cudaMemPoolTrimTo(ctx->pool, 0);
@@ -901,6 +910,115 @@ extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_
     if (state) state_free(state);
     for (int i = 0; i < 12; ++i) pool_free(d[i], stream);
     return code;
+}
+
+extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, const cs_camera *cam,
+                                         const cs_settings *settings, const float *dL_host, float *image_host,
+                                         float *dpoints_host, float *ddelta_host, float *dsigma_host,
+                                         float *dopacity_host, float *dsh_host, uint64_t *ticket) {
+    if (!ctx || !ticket) return fail(CS_ERR_ARG, "cs_step_host_submit: context and ticket are required");
+    cs_status st;
+    if ((st = check_scene(sh)) != CS_OK) return st;
+    if (!cam || !image_host) return fail(CS_ERR_ARG, "cs_step_host_submit: camera and image are required");
+    if ((st = check_camera(cam)) != CS_OK) return st;
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->host_mu);
+    const bool bwd = dL_host != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->upload_stream) {
+        e = cudaStreamCreateWithFlags(&ctx->upload_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->compute_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->download_stream, cudaStreamNonBlocking);
+        for (auto &sl : ctx->host_slots) {
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: streams and events");
+    }
+    const uint64_t t = ctx->host_tickets + 1;
+    cs_context::HostSlot &sl = ctx->host_slots[t & 1];
+    // the slot's arrays: 0-4 scene (as stored), 5 dL/dimage, 6 image, 7-11 gradients (binary32)
+    const int64_t n = sh->n;
+    const int nb = (sh->sh_degree + 1) * (sh->sh_degree + 1);
+    const size_t esz = sh->storage == CS_STORE_F32 ? 4 : 2;
+    const size_t e_pts = (size_t)n * sh->k * 3, e_one = (size_t)n, e_sh = (size_t)n * nb * 3;
+    const size_t b_img = (size_t)3 * cam->width * cam->height * 4;
+    const size_t sizes[12] = {e_pts * esz, e_one * esz, e_one * esz, e_one * esz, e_sh * esz, bwd ? b_img : 0,
+                              b_img,       e_pts * 4,   e_one * 4,   e_one * 4,   e_one * 4, e_sh * 4};
+    float *outs_host[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
+    size_t offs[12], total = 0;
+    for (int i = 0; i < 12; ++i) {
+        offs[i] = total;
+        const bool used = i < 7 || (bwd && outs_host[i - 7]);
+        total += used ? (sizes[i] + 255) & ~(size_t)255 : 0;
+    }
+    if (sl.cap < total) {  // the slot's last step must be done with its buffers before they are replaced
+        if (sl.ticket) e = cudaEventSynchronize(sl.done);
+        if (sl.buf) cudaFree(sl.buf);
+        sl.buf = nullptr;
+        sl.cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&sl.buf, total);
+        if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: slot buffers");
+        sl.cap = total;
+    }
+    void *d[12];
+    for (int i = 0; i < 12; ++i) d[i] = static_cast<char *>(sl.buf) + offs[i];
+    // inputs: the copy into this slot waits (on the GPU) until the slot's previous step has read them
+    if (sl.ticket) e = cudaStreamWaitEvent(ctx->upload_stream, sl.computed, 0);
+    const void *srcs[6] = {sh->points, sh->delta, sh->sigma, sh->opacity, sh->sh, dL_host};
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+        if (sizes[i]) e = cudaMemcpyAsync(d[i], srcs[i], sizes[i], cudaMemcpyHostToDevice, ctx->upload_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.uploaded, ctx->upload_stream);
+    // the step: after its inputs, and after the slot's previous outputs have been copied out
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->compute_stream, sl.uploaded, 0);
+    if (e == cudaSuccess && sl.ticket) e = cudaStreamWaitEvent(ctx->compute_stream, sl.done, 0);
+    if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: upload");
+    cs_scene dev = *sh;
+    dev.points = static_cast<float *>(d[0]);
+    dev.delta = static_cast<float *>(d[1]);
+    dev.sigma = static_cast<float *>(d[2]);
+    dev.opacity = static_cast<float *>(d[3]);
+    dev.sh = static_cast<float *>(d[4]);
+    float *g[5];
+    for (int i = 0; i < 5; ++i) g[i] = bwd && outs_host[i] ? static_cast<float *>(d[7 + i]) : nullptr;
+    cs_fwd_state *state = nullptr;
+    cs_status code = cs_forward(ctx, &dev, cam, 1, settings, static_cast<float *>(d[6]), nullptr,
+                                bwd ? &state : nullptr, ctx->compute_stream);
+    if (code == CS_OK && bwd)
+        code = cs_backward_write(ctx, state, static_cast<const float *>(d[5]), g[0], g[1], g[2], g[3], g[4],
+                                 ctx->compute_stream);
+    if (state) state_free(state);
+    // recorded whatever happened above, so that no later wait waits on nothing
+    e = cudaEventRecord(sl.computed, ctx->compute_stream);
+    // outputs: copied out while the next step computes
+    cudaError_t e2 = cudaStreamWaitEvent(ctx->download_stream, sl.computed, 0);
+    if (e2 == cudaSuccess && code == CS_OK)
+        e2 = cudaMemcpyAsync(image_host, d[6], b_img, cudaMemcpyDeviceToHost, ctx->download_stream);
+    for (int i = 0; i < 5 && e2 == cudaSuccess && code == CS_OK; ++i)
+        if (g[i] && sizes[7 + i])
+            e2 = cudaMemcpyAsync(outs_host[i], g[i], sizes[7 + i], cudaMemcpyDeviceToHost, ctx->download_stream);
+    const cudaError_t e3 = cudaEventRecord(sl.done, ctx->download_stream);
+    sl.ticket = t;
+    ctx->host_tickets = t;
+    *ticket = t;
+    if (code == CS_OK && e != cudaSuccess) code = fail_cuda(e, "cs_step_host_submit");
+    if (code == CS_OK && e2 != cudaSuccess) code = fail_cuda(e2, "cs_step_host_submit: download");
+    if (code == CS_OK && e3 != cudaSuccess) code = fail_cuda(e3, "cs_step_host_submit");
+    return code;
+}
+
+extern "C" cs_status cs_step_host_wait(cs_context *ctx, uint64_t ticket) {
+    if (!ctx) return fail(CS_ERR_ARG, "context is NULL");
+    DeviceGuard dg(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->host_mu);
+    if (ticket == 0 || ticket > ctx->host_tickets)
+        return fail(CS_ERR_ARG, "cs_step_host_wait: ticket %llu was not submitted", (unsigned long long)ticket);
+    // steps are copied out in order on the download stream, and the step last recorded in the
+    // ticket's slot is this one or a later one
+    const cudaError_t e = cudaEventSynchronize(ctx->host_slots[ticket & 1].done);
+    if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_wait");
+    return take_device_status(ctx->compute_stream, "cs_step_host_wait");
 }
 
 extern "C" cs_status cs_work_counts(cs_context *ctx, const cs_fwd_state *s, const float *dL_dimage, uint64_t *counts,

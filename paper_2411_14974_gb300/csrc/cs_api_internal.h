@@ -23,6 +23,19 @@ struct cs_context {
     std::mutex prof_mu;
     std::vector<StageRec> prof;
     std::vector<cudaEvent_t> free_events;
+    // pipelined host-buffer steps (cs_step_host_submit): two slots of device buffers (scene,
+    // cotangent, image, gradients); a step's inputs are copied in on the upload stream and its
+    // outputs copied out on the download stream while the other slot's step computes
+    struct HostSlot {
+        void *buf = nullptr;  // the slot's twelve arrays, 256-byte aligned
+        size_t cap = 0;
+        cudaEvent_t uploaded = nullptr, computed = nullptr, done = nullptr;
+        uint64_t ticket = 0;  // the last step submitted into this slot (0: none)
+    };
+    HostSlot host_slots[2];
+    cudaStream_t upload_stream = nullptr, compute_stream = nullptr, download_stream = nullptr;
+    uint64_t host_tickets = 0;
+    std::mutex host_mu;
 };
 
 struct cs_fwd_state {

@@ -536,6 +536,42 @@ def step_host(scene_host: dict, sh_degree: int, cams: Sequence, settings: Option
     B.check(code, "cs_step_host")
 
 
+def _host_scene_struct(scene_host: dict, sh_degree: int):
+    sc = B.CsScene()
+    for name in ("points", "delta", "sigma", "opacity", "sh"):
+        t = scene_host[name]
+        setattr(sc, name, t.data_ptr() if t.numel() else None)
+    sc.n = int(scene_host["points"].shape[0])
+    sc.k = int(scene_host["points"].shape[1])
+    sc.sh_degree = int(sh_degree)
+    sc.activation = 1 if scene_host.get("raw", False) else 0
+    sc.storage = _STORAGE[scene_host["points"].dtype]
+    return sc
+
+
+def step_host_submit(scene_host: dict, sh_degree: int, cam, settings: Optional[Settings], dL_host, image_host,
+                     grads_host: Optional[dict] = None, device: int = 0) -> int:
+    """cs_step_host_submit: enqueue one host-buffer step of one view; returns its ticket.  The host
+    tensors (pinned for overlap) must stay untouched until step_host_wait(ticket)."""
+    ctx = Context.get(device)
+    sc = _host_scene_struct(scene_host, sh_degree)
+    s = (settings or Settings()).struct()
+    g = grads_host or {}
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    ticket = ctypes.c_uint64(0)
+    code = B.lib().cs_step_host_submit(ctx.handle, ctypes.byref(sc), cameras_array([cam]), ctypes.byref(s),
+                                       ptr(dL_host), image_host.data_ptr(), ptr(g.get("points")),
+                                       ptr(g.get("delta")), ptr(g.get("sigma")), ptr(g.get("opacity")),
+                                       ptr(g.get("sh")), ctypes.byref(ticket))
+    B.check(code, "cs_step_host_submit")
+    return int(ticket.value)
+
+
+def step_host_wait(ticket: int, device: int = 0) -> None:
+    """cs_step_host_wait: block until the submitted step `ticket` (and every earlier one) is done."""
+    B.check(B.lib().cs_step_host_wait(Context.get(device).handle, ctypes.c_uint64(ticket)), "cs_step_host_wait")
+
+
 # ---- serving -----------------------------------------------------------------------------------
 class Server:
     """Continuous-batching view server over resident scenes (cs_server_* in the C ABI).

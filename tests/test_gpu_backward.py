@@ -313,3 +313,43 @@ def test_step_through_host_buffers_equals_device_calls(pinned, n_views):
         a, b = g_h[f].numpy(), want[f].cpu().numpy()
         assert np.isfinite(a).all(), f
         assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-30), f
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pipelined_host_steps_equal_device_calls(pinned):
+    """cs_step_host_submit / cs_step_host_wait: three steps submitted back to back (each step's
+    inputs copied in and outputs copied out while the other slot's step computes) give, view by
+    view, the image of cs_forward bit for bit and the gradients of cs_backward up to the order of
+    the atomics, from pinned or pageable host memory; a ticket that was never submitted is
+    rejected."""
+    import torch
+    import paper_2411_14974_gb300 as cs
+    from paper_2411_14974_gb300 import _binding as B
+    sc = syn.surface_scene(67, n=6_000, sh_degree=2)
+    cams = syn.sphere_cameras(3, 80, 64, 4.0, seed=68)
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    G = np.random.default_rng(69).uniform(-1, 1, (3, 1, 3, 64, 80)).astype(np.float32)
+    pin = lambda a: (torch.as_tensor(np.ascontiguousarray(a, np.float32)).pin_memory() if pinned
+                     else torch.as_tensor(np.ascontiguousarray(a, np.float32)))
+    scene_h = dict(points=pin(sc.points), delta=pin(sc.delta), sigma=pin(sc.sigma), opacity=pin(sc.opacity),
+                   sh=pin(sc.sh))
+    imgs = [pin(np.full((1, 3, 64, 80), np.nan)) for _ in cams]
+    gs = [{f: pin(np.full(tuple(getattr(t, f).shape), np.nan)) for f in FIELDS} for _ in cams]
+    dls = [pin(G[v]) for v in range(3)]
+    tickets = [cs.step_host_submit(scene_h, sc.sh_degree, cam, cs.Settings(), dls[v], imgs[v], gs[v])
+               for v, cam in enumerate(cams)]
+    assert tickets == sorted(tickets) and len(set(tickets)) == 3
+    cs.step_host_wait(tickets[-1])
+    for v, cam in enumerate(cams):
+        img, _, state = cs.forward(t, [cam], cs.Settings(), keep_state=True)
+        want = cs.backward(state, torch.as_tensor(G[v], device=dev))
+        torch.cuda.synchronize()
+        state.release()
+        assert torch.equal(imgs[v], img.cpu()), v
+        for f in FIELDS:
+            a, b = gs[v][f].numpy(), want[f].cpu().numpy()
+            assert np.isfinite(a).all(), (v, f)
+            assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-30), (v, f)
+    with pytest.raises(B.CsError):
+        cs.step_host_wait(tickets[-1] + 100)
