@@ -223,21 +223,26 @@ cs_status cs_step_host(cs_context *ctx, const cs_scene *scene_host, const cs_cam
                        float *dsh_host, void *stream);
 
 /* Pipelined host-buffer steps (no counterpart in the paper).  cs_step_host_submit enqueues the work
-   of cs_step_host for one view and returns a ticket without waiting for the step to end.  The
-   context keeps two slots of device buffers (scene, dL_dimage, image, gradients) and three
-   streams of its own: a step's scene and dL_dimage are copied into its slot on the upload stream,
-   the step computes on the compute stream, and its image and gradients are copied out on the
-   download stream, so that one step's outputs leave and the next step's inputs arrive over the
-   host link while the GPU computes.  The call still waits mid-way for the step's own preprocess
-   (the forward's host synchronisation on the pair count), i.e. until the step's scene has arrived
-   and its records are computed.  The host buffers should be pinned (or registered): a copy to or
-   from pageable memory makes the call wait for it.  The gradients are written, not accumulated;
-   any gradient pointer may be NULL, and dL_dimage NULL runs the forward only.  Until
-   cs_step_host_wait(ticket) returns, the step's host arrays must not change and its outputs must
-   not be read.  Steps complete in submission order: waiting for a ticket waits for every earlier
-   step of the context too.  The slots (cudaMalloc'd, grown to the largest step submitted) and the
-   streams are kept until cs_context_destroy.  Errors: CS_ERR_ARG (also for a ticket not yet
-   submitted), CS_ERR_CUDA, and those of cs_forward and cs_backward_write. */
+   of cs_step_host for one view and returns a ticket without waiting for any of it.  The context
+   keeps three slots of device buffers (scene, dL_dimage, image, gradients), three streams and one
+   worker thread of its own: the calling thread copies a step's scene and dL_dimage into its slot
+   on the upload stream and queues the step; the worker thread enqueues the step's forward and
+   backward on the compute stream (it, not the caller, waits there for the forward's pair count)
+   and the copies of its image and gradients on the download stream.  So later steps' inputs
+   arrive and earlier steps' outputs leave over the host link while the GPU computes.  A submit
+   waits only when the step three tickets back has not yet been enqueued by the worker (its slot
+   is reused).  The host buffers should be pinned (or registered): a copy to or from pageable
+   memory makes the call wait for it.  The gradients are written, not accumulated; any gradient
+   pointer may be NULL, and dL_dimage NULL runs the forward only.  Until cs_step_host_wait(ticket)
+   returns, the step's host arrays must not change and its outputs must not be read, and the
+   context must be given no call other than cs_step_host_submit and cs_step_host_wait.  Steps
+   complete in submission order: waiting for a ticket waits for every earlier step of the context
+   too.  The slots (cudaMalloc'd, grown to the largest step submitted), the streams and the thread
+   are kept until cs_context_destroy, which lets the thread enqueue the steps still queued and
+   waits for them.  Errors: the submit reports argument errors (CS_ERR_ARG, also for a ticket not
+   yet submitted) and failures of the upload (CS_ERR_CUDA); a failure of a queued step's forward,
+   backward or download (the codes of cs_forward and cs_backward_write) is returned, with its
+   message, by the next cs_step_host_wait, once. */
 cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *scene_host, const cs_camera *cam,
                               const cs_settings *settings, const float *dL_dimage_host, float *image_host,
                               float *dpoints_host, float *ddelta_host, float *dsigma_host, float *dopacity_host,

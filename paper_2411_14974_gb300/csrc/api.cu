@@ -152,7 +152,9 @@ extern "C" cs_status cs_context_create(int32_t device, cs_context **out) {
     }
     uint64_t keep = UINT64_MAX;  // keep freed memory in the pool: later calls reuse it without the driver
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    e = cudaMallocHost(&c->host_total, sizeof(unsigned long long) * 8);
+    // the readback slots are written by a kernel (no copy engine), through their device address
+    e = cudaHostAlloc(&c->host_total, sizeof(unsigned long long) * 8, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&c->host_total_dev, c->host_total, 0);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->totals_ready, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->host_total) cudaFreeHost(c->host_total);
@@ -177,6 +179,15 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
+    if (ctx->host_worker.joinable()) {  // the worker enqueues what is queued, then ends
+        {
+            std::lock_guard<std::mutex> lk(ctx->job_mu);
+            ctx->worker_stop = true;
+        }
+        ctx->job_cv.notify_all();
+        ctx->host_worker.join();
+        cudaDeviceSynchronize();
+    }
     for (auto &sl : ctx->host_slots) {
         if (sl.buf) cudaFree(sl.buf);
         if (sl.uploaded) cudaEventDestroy(sl.uploaded);
@@ -202,7 +213,7 @@ cudaError_t cs::pool_alloc(cs_context *ctx, void **p, size_t bytes, cudaStream_t
 #if CS_CHECKED
     // checked builds hand out every buffer filled with 0xff bytes (NaN as float): a read of a
     // buffer before it is written then shows in the results
-    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0xff, bytes, s);
+    if (e == cudaSuccess) e = fill_words(*p, 0xffffffffu, bytes, s);
 #endif
     return e;
 }
@@ -416,10 +427,9 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
             off += np;
         }
     }
-    CS_TRY(cudaMemcpyAsync(s->views_dev, s->views.data(), sizeof(ViewDesc) * V, cudaMemcpyHostToDevice, stream),
-           "copy views");
+    CS_TRY(put_views(s->views_dev, s->views.data(), V, stream), "copy views");
     CS_TRY(pool_alloc(ctx, (void **)&total, sizeof(PreprocessStats), stream), "alloc");
-    CS_TRY(cudaMemsetAsync(total, 0, sizeof(PreprocessStats), stream), "clear totals");
+    CS_TRY(fill_words(total, 0u, sizeof(PreprocessStats), stream), "clear totals");
     {
         StageTimer tm(ctx, CS_STAGE_PREPROCESS, stream);
         PreprocessOut po{s->records, s->depth_keys, s->rects, s->counts, s->bboxes, radii,
@@ -441,8 +451,7 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     // of the drawn records' depth keys; the depth sort orders only the low bits in which they differ
     // (the drawn keys share the others; undrawn records emit no pairs).  Its first pass, on key bits
     // 0-7, needs neither, so it runs on the device while the host waits for the totals.
-    CS_TRY(cudaMemcpyAsync(ctx->host_total, total, sizeof(PreprocessStats), cudaMemcpyDeviceToHost, stream),
-           "read totals");
+    CS_TRY(publish_words(total, ctx->host_total_dev, (int)(sizeof(PreprocessStats) / 4), stream), "read totals");
     CS_TRY(cudaEventRecord(ctx->totals_ready, stream), "record");
     if (R > 1) {
         StageTimer tm(ctx, CS_STAGE_DEPTH_SORT, stream);
@@ -553,14 +562,14 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&cnt, 2 * sizeof(unsigned int), stream);
         if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&stmp, scan_tmp_words(tiles) * 8, stream);
         if (e == cudaSuccess) e = pool_alloc(ctx, (void **)&s->split_slot, (size_t)tiles * 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned int), stream);
+        if (e == cudaSuccess) e = fill_words(cnt, 0u, 2 * sizeof(unsigned int), stream);
         if (e == cudaSuccess) e = launch_split_count(s->ranges, tiles, split, heavy, light, cnt, stream);
         if (e == cudaSuccess) e = launch_exclusive_scan(heavy, nullptr, heavy_base, tiles, tot, stmp, stream);
         if (e == cudaSuccess) e = launch_exclusive_scan(light, nullptr, light_base, tiles, tot + 1, stmp, stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->host_total, tot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+            e = publish_words(tot, ctx->host_total_dev, 4, stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->host_total + 2, cnt, sizeof(unsigned int), cudaMemcpyDeviceToHost, stream);
+            e = publish_words(cnt, ctx->host_total_dev + 2, 1, stream);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->totals_ready, stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ctx->totals_ready);
         uint64_t n_slots = 0, n_light = 0, n_heavy = 0;
@@ -724,18 +733,18 @@ static cs_status run_backward(cs_context *ctx, const cs_fwd_state *s, const floa
         const int64_t n = s->scene.n;
         const int64_t nb = (int64_t)(s->scene.sh_degree + 1) * (s->scene.sh_degree + 1);
         cudaError_t e = cudaSuccess;
-        if (dpoints) e = cudaMemsetAsync(dpoints, 0, (size_t)n * s->k * 3 * 4, stream);
-        if (e == cudaSuccess && ddelta) e = cudaMemsetAsync(ddelta, 0, (size_t)n * 4, stream);
-        if (e == cudaSuccess && dsigma) e = cudaMemsetAsync(dsigma, 0, (size_t)n * 4, stream);
-        if (e == cudaSuccess && dopacity) e = cudaMemsetAsync(dopacity, 0, (size_t)n * 4, stream);
-        if (e == cudaSuccess && dsh) e = cudaMemsetAsync(dsh, 0, (size_t)(n * nb * 3) * 4, stream);
+        if (dpoints) e = fill_words(dpoints, 0u, (size_t)n * s->k * 3 * 4, stream);
+        if (e == cudaSuccess && ddelta) e = fill_words(ddelta, 0u, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dsigma) e = fill_words(dsigma, 0u, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dopacity) e = fill_words(dopacity, 0u, (size_t)n * 4, stream);
+        if (e == cudaSuccess && dsh) e = fill_words(dsh, 0u, (size_t)(n * nb * 3) * 4, stream);
         if (e != cudaSuccess) return fail_cuda(e, "clear gradients");
     }
     if (s->n_records == 0) return CS_OK;
     {
         cudaError_t e = pool_alloc(ctx, (void **)&grads, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e != cudaSuccess) return fail_cuda(e, "alloc gradient records");
-        e = cudaMemsetAsync(grads, 0, (size_t)s->n_records * GRAD_WORDS * 4, stream);
+        e = fill_words(grads, 0u, (size_t)s->n_records * GRAD_WORDS * 4, stream);
         if (e == cudaSuccess) {
             StageTimer tm(ctx, CS_STAGE_BLEND_BACKWARD, stream);
             BlendArgs a{s->views_dev, V, s->ranges, s->pair_vals, s->records, s->bboxes, s->st, s->n_tiles, s->k,
@@ -912,6 +921,72 @@ extern "C" cs_status cs_step_host(cs_context *ctx, const cs_scene *sh, const cs_
     return code;
 }
 
+// The worker thread of the pipelined host-buffer steps: takes the queued steps in ticket order and
+// enqueues, for each, the forward and backward on the compute stream (after its upload, and after
+// the slot's previous outputs have been copied out) and the copies of its outputs on the download
+// stream.  The forward's pair-count readback blocks this thread, not the caller's.
+static void host_worker_loop(cs_context *ctx) {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        cs_context::HostJob job;
+        {
+            std::unique_lock<std::mutex> lk(ctx->job_mu);
+            ctx->job_cv.wait(lk, [&] { return ctx->worker_stop || !ctx->jobs.empty(); });
+            if (ctx->jobs.empty()) return;  // stopping, nothing left
+            job = ctx->jobs.front();
+            ctx->jobs.pop_front();
+        }
+        cs_context::HostSlot &sl = ctx->host_slots[job.slot];
+        cs_status code = CS_OK;
+        cudaError_t e = cudaStreamWaitEvent(ctx->compute_stream, sl.uploaded, 0);
+        // the slot's previous step (ticket - HOST_SLOTS), if any, was enqueued before this one:
+        // its outputs must be copied out before this step writes over them
+        if (e == cudaSuccess && job.ticket > (uint64_t)cs_context::HOST_SLOTS)
+            e = cudaStreamWaitEvent(ctx->compute_stream, sl.done, 0);
+        if (e != cudaSuccess) code = fail_cuda(e, "cs_step_host_submit: stream order");
+        float *g[5];
+        for (int i = 0; i < 5; ++i)
+            g[i] = job.bwd && job.outs_host[i] ? static_cast<float *>(job.d[7 + i]) : nullptr;
+        cs_fwd_state *state = nullptr;
+        if (code == CS_OK)
+            code = cs_forward(ctx, &job.scene, &job.cam, 1, job.has_settings ? &job.settings : nullptr,
+                              static_cast<float *>(job.d[6]), nullptr, job.bwd ? &state : nullptr,
+                              ctx->compute_stream);
+        if (code == CS_OK && job.bwd)
+            code = cs_backward_write(ctx, state, static_cast<const float *>(job.d[5]), g[0], g[1], g[2], g[3], g[4],
+                                     ctx->compute_stream);
+        if (state) state_free(state);
+        // recorded whatever happened above, so that no later wait waits on an older step
+        e = cudaEventRecord(sl.computed, ctx->compute_stream);
+        cudaError_t e2 = cudaStreamWaitEvent(ctx->download_stream, sl.computed, 0);
+        if (e2 == cudaSuccess && code == CS_OK)
+            e2 = cudaMemcpyAsync(job.image_host, job.d[6], job.sizes[6], cudaMemcpyDeviceToHost, ctx->download_stream);
+        for (int i = 0; i < 5 && e2 == cudaSuccess && code == CS_OK; ++i)
+            if (g[i] && job.sizes[7 + i])
+                e2 = cudaMemcpyAsync(job.outs_host[i], g[i], job.sizes[7 + i], cudaMemcpyDeviceToHost,
+                                     ctx->download_stream);
+        const cudaError_t e3 = cudaEventRecord(sl.done, ctx->download_stream);
+        if (code == CS_OK && e != cudaSuccess) code = fail_cuda(e, "cs_step_host_submit");
+        if (code == CS_OK && e2 != cudaSuccess) code = fail_cuda(e2, "cs_step_host_submit: download");
+        if (code == CS_OK && e3 != cudaSuccess) code = fail_cuda(e3, "cs_step_host_submit");
+        {
+            std::lock_guard<std::mutex> lk(ctx->job_mu);
+            if (code != CS_OK && ctx->host_code == CS_OK) {
+                ctx->host_code = code;
+                ctx->host_msg = cs_last_error();
+            }
+            ctx->jobs_enqueued = job.ticket;
+        }
+        ctx->job_cv.notify_all();
+    }
+}
+
+// blocks until the worker has enqueued the GPU work of every step up to `ticket`
+static void wait_enqueued(cs_context *ctx, uint64_t ticket) {
+    std::unique_lock<std::mutex> lk(ctx->job_mu);
+    ctx->job_cv.wait(lk, [&] { return ctx->jobs_enqueued >= ticket; });
+}
+
 extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, const cs_camera *cam,
                                          const cs_settings *settings, const float *dL_host, float *image_host,
                                          float *dpoints_host, float *ddelta_host, float *dsigma_host,
@@ -921,6 +996,7 @@ extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, co
     if ((st = check_scene(sh)) != CS_OK) return st;
     if (!cam || !image_host) return fail(CS_ERR_ARG, "cs_step_host_submit: camera and image are required");
     if ((st = check_camera(cam)) != CS_OK) return st;
+    if (settings && (st = check_settings(settings)) != CS_OK) return st;
     DeviceGuard dg(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->host_mu);
     const bool bwd = dL_host != nullptr;
@@ -935,9 +1011,28 @@ extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, co
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         }
         if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: streams and events");
+        try {
+            ctx->host_worker = std::thread(host_worker_loop, ctx);
+        } catch (...) {
+            return fail(CS_ERR_CUDA, "cs_step_host_submit: cannot start the worker thread");
+        }
     }
     const uint64_t t = ctx->host_tickets + 1;
-    cs_context::HostSlot &sl = ctx->host_slots[t & 1];
+    const int slot = (int)(t % cs_context::HOST_SLOTS);
+    cs_context::HostSlot &sl = ctx->host_slots[slot];
+    // the slot's previous step must have its GPU work enqueued (its events recorded) before this
+    // step's copies are ordered after them
+    if (sl.ticket) wait_enqueued(ctx, sl.ticket);
+    cs_context::HostJob job;
+    job.ticket = t;
+    job.slot = slot;
+    job.bwd = bwd;
+    job.cam = *cam;
+    job.has_settings = settings != nullptr;
+    if (settings) job.settings = *settings;
+    job.image_host = image_host;
+    float *outs_host[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
+    for (int i = 0; i < 5; ++i) job.outs_host[i] = outs_host[i];
     // the slot's arrays: 0-4 scene (as stored), 5 dL/dimage, 6 image, 7-11 gradients (binary32)
     const int64_t n = sh->n;
     const int nb = (sh->sh_degree + 1) * (sh->sh_degree + 1);
@@ -946,10 +1041,10 @@ extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, co
     const size_t b_img = (size_t)3 * cam->width * cam->height * 4;
     const size_t sizes[12] = {e_pts * esz, e_one * esz, e_one * esz, e_one * esz, e_sh * esz, bwd ? b_img : 0,
                               b_img,       e_pts * 4,   e_one * 4,   e_one * 4,   e_one * 4, e_sh * 4};
-    float *outs_host[5] = {dpoints_host, ddelta_host, dsigma_host, dopacity_host, dsh_host};
     size_t offs[12], total = 0;
     for (int i = 0; i < 12; ++i) {
         offs[i] = total;
+        job.sizes[i] = sizes[i];
         const bool used = i < 7 || (bwd && outs_host[i - 7]);
         total += used ? (sizes[i] + 255) & ~(size_t)255 : 0;
     }
@@ -962,50 +1057,29 @@ extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, co
         if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: slot buffers");
         sl.cap = total;
     }
-    void *d[12];
-    for (int i = 0; i < 12; ++i) d[i] = static_cast<char *>(sl.buf) + offs[i];
+    for (int i = 0; i < 12; ++i) job.d[i] = static_cast<char *>(sl.buf) + offs[i];
     // inputs: the copy into this slot waits (on the GPU) until the slot's previous step has read them
     if (sl.ticket) e = cudaStreamWaitEvent(ctx->upload_stream, sl.computed, 0);
     const void *srcs[6] = {sh->points, sh->delta, sh->sigma, sh->opacity, sh->sh, dL_host};
     for (int i = 0; i < 6 && e == cudaSuccess; ++i)
-        if (sizes[i]) e = cudaMemcpyAsync(d[i], srcs[i], sizes[i], cudaMemcpyHostToDevice, ctx->upload_stream);
+        if (sizes[i]) e = cudaMemcpyAsync(job.d[i], srcs[i], sizes[i], cudaMemcpyHostToDevice, ctx->upload_stream);
     if (e == cudaSuccess) e = cudaEventRecord(sl.uploaded, ctx->upload_stream);
-    // the step: after its inputs, and after the slot's previous outputs have been copied out
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->compute_stream, sl.uploaded, 0);
-    if (e == cudaSuccess && sl.ticket) e = cudaStreamWaitEvent(ctx->compute_stream, sl.done, 0);
     if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: upload");
-    cs_scene dev = *sh;
-    dev.points = static_cast<float *>(d[0]);
-    dev.delta = static_cast<float *>(d[1]);
-    dev.sigma = static_cast<float *>(d[2]);
-    dev.opacity = static_cast<float *>(d[3]);
-    dev.sh = static_cast<float *>(d[4]);
-    float *g[5];
-    for (int i = 0; i < 5; ++i) g[i] = bwd && outs_host[i] ? static_cast<float *>(d[7 + i]) : nullptr;
-    cs_fwd_state *state = nullptr;
-    cs_status code = cs_forward(ctx, &dev, cam, 1, settings, static_cast<float *>(d[6]), nullptr,
-                                bwd ? &state : nullptr, ctx->compute_stream);
-    if (code == CS_OK && bwd)
-        code = cs_backward_write(ctx, state, static_cast<const float *>(d[5]), g[0], g[1], g[2], g[3], g[4],
-                                 ctx->compute_stream);
-    if (state) state_free(state);
-    // recorded whatever happened above, so that no later wait waits on nothing
-    e = cudaEventRecord(sl.computed, ctx->compute_stream);
-    // outputs: copied out while the next step computes
-    cudaError_t e2 = cudaStreamWaitEvent(ctx->download_stream, sl.computed, 0);
-    if (e2 == cudaSuccess && code == CS_OK)
-        e2 = cudaMemcpyAsync(image_host, d[6], b_img, cudaMemcpyDeviceToHost, ctx->download_stream);
-    for (int i = 0; i < 5 && e2 == cudaSuccess && code == CS_OK; ++i)
-        if (g[i] && sizes[7 + i])
-            e2 = cudaMemcpyAsync(outs_host[i], g[i], sizes[7 + i], cudaMemcpyDeviceToHost, ctx->download_stream);
-    const cudaError_t e3 = cudaEventRecord(sl.done, ctx->download_stream);
+    job.scene = *sh;
+    job.scene.points = static_cast<float *>(job.d[0]);
+    job.scene.delta = static_cast<float *>(job.d[1]);
+    job.scene.sigma = static_cast<float *>(job.d[2]);
+    job.scene.opacity = static_cast<float *>(job.d[3]);
+    job.scene.sh = static_cast<float *>(job.d[4]);
     sl.ticket = t;
     ctx->host_tickets = t;
+    {
+        std::lock_guard<std::mutex> jl(ctx->job_mu);
+        ctx->jobs.push_back(job);
+    }
+    ctx->job_cv.notify_all();
     *ticket = t;
-    if (code == CS_OK && e != cudaSuccess) code = fail_cuda(e, "cs_step_host_submit");
-    if (code == CS_OK && e2 != cudaSuccess) code = fail_cuda(e2, "cs_step_host_submit: download");
-    if (code == CS_OK && e3 != cudaSuccess) code = fail_cuda(e3, "cs_step_host_submit");
-    return code;
+    return CS_OK;
 }
 
 extern "C" cs_status cs_step_host_wait(cs_context *ctx, uint64_t ticket) {
@@ -1014,9 +1088,18 @@ extern "C" cs_status cs_step_host_wait(cs_context *ctx, uint64_t ticket) {
     std::lock_guard<std::mutex> lk(ctx->host_mu);
     if (ticket == 0 || ticket > ctx->host_tickets)
         return fail(CS_ERR_ARG, "cs_step_host_wait: ticket %llu was not submitted", (unsigned long long)ticket);
+    wait_enqueued(ctx, ticket);
     // steps are copied out in order on the download stream, and the step last recorded in the
     // ticket's slot is this one or a later one
-    const cudaError_t e = cudaEventSynchronize(ctx->host_slots[ticket & 1].done);
+    const cudaError_t e = cudaEventSynchronize(ctx->host_slots[ticket % cs_context::HOST_SLOTS].done);
+    {
+        std::lock_guard<std::mutex> jl(ctx->job_mu);
+        if (ctx->host_code != CS_OK) {  // reported once, with the worker's message
+            const cs_status code = ctx->host_code;
+            ctx->host_code = CS_OK;
+            return fail(code, "%s", ctx->host_msg.c_str());
+        }
+    }
     if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_wait");
     return take_device_status(ctx->compute_stream, "cs_step_host_wait");
 }

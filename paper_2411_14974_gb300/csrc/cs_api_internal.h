@@ -3,7 +3,11 @@
 
 #include <cuda_runtime.h>
 
+#include <condition_variable>
+#include <deque>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "cs_common.cuh"
@@ -13,6 +17,7 @@ struct cs_context {
     int sm_count = 0;
     cudaMemPool_t pool = nullptr;             // stream-ordered pool for every transient buffer
     unsigned long long *host_total = nullptr; // pinned readback slots (8 words): the forward's totals
+    unsigned long long *host_total_dev = nullptr;  // the same slots in the device's address space
     cudaEvent_t totals_ready = nullptr;       // recorded after the readback of the forward's totals
     // stage profiling: events recorded on the launching stream around every stage
     bool profiling = false;
@@ -23,19 +28,44 @@ struct cs_context {
     std::mutex prof_mu;
     std::vector<StageRec> prof;
     std::vector<cudaEvent_t> free_events;
-    // pipelined host-buffer steps (cs_step_host_submit): two slots of device buffers (scene,
-    // cotangent, image, gradients); a step's inputs are copied in on the upload stream and its
-    // outputs copied out on the download stream while the other slot's step computes
+    // pipelined host-buffer steps (cs_step_host_submit): HOST_SLOTS slots of device buffers
+    // (scene, cotangent, image, gradients).  The caller's thread copies a step's inputs into its
+    // slot on the upload stream and queues the step; the context's worker thread enqueues the
+    // step's forward and backward on the compute stream (waiting there for the forward's pair
+    // count) and the copies of its outputs on the download stream.  Uploads of later steps, the
+    // compute of one step and downloads of earlier ones thus run at the same time.
+    static constexpr int HOST_SLOTS = 3;
     struct HostSlot {
         void *buf = nullptr;  // the slot's twelve arrays, 256-byte aligned
         size_t cap = 0;
         cudaEvent_t uploaded = nullptr, computed = nullptr, done = nullptr;
         uint64_t ticket = 0;  // the last step submitted into this slot (0: none)
     };
-    HostSlot host_slots[2];
+    struct HostJob {          // one queued step, its inputs already on the upload stream
+        uint64_t ticket = 0;
+        int slot = 0;
+        bool bwd = false;
+        bool has_settings = false;
+        cs_scene scene{};     // the slot's device copies of the scene
+        cs_camera cam{};
+        cs_settings settings{};
+        float *image_host = nullptr;
+        float *outs_host[5] = {};
+        void *d[12] = {};
+        size_t sizes[12] = {};
+    };
+    HostSlot host_slots[HOST_SLOTS];
     cudaStream_t upload_stream = nullptr, compute_stream = nullptr, download_stream = nullptr;
     uint64_t host_tickets = 0;
-    std::mutex host_mu;
+    std::mutex host_mu;                 // one submit or wait at a time
+    std::thread host_worker;
+    std::mutex job_mu;                  // guards the queue and the fields below
+    std::condition_variable job_cv;
+    std::deque<HostJob> jobs;
+    bool worker_stop = false;
+    uint64_t jobs_enqueued = 0;         // every step up to this ticket has its GPU work enqueued
+    cs_status host_code = CS_OK;        // first failure of a queued step since the last report
+    std::string host_msg;
 };
 
 struct cs_fwd_state {

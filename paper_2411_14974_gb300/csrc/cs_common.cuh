@@ -207,6 +207,15 @@ cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned lo
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,
                                   float4 *grad_records, cudaStream_t s, unsigned long long *counts = nullptr);
 
+// Small transfers done by kernels, never by a copy engine (transfer.cu): the words of p (4-byte
+// aligned, bytes a multiple of 4) set to v; n view descriptors copied from host memory (read when
+// the call is made) to device memory; `words` 32-bit words copied from device memory to pinned
+// host memory mapped into the device's address space (visible to the host once the stream has
+// reached the end of the kernel)
+cudaError_t fill_words(void *p, uint32_t v, size_t bytes, cudaStream_t s);
+cudaError_t put_views(ViewDesc *dst, const ViewDesc *src, int n, cudaStream_t s);
+cudaError_t publish_words(const void *src, void *dst_host_mapped, int words, cudaStream_t s);
+
 // process-wide count of kernel launches made by the library
 void count_launches(int n);
 

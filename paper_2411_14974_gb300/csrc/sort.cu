@@ -544,7 +544,7 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, const uint32_t *gather, ui
                                   unsigned long long *total_dev, unsigned long long *tmp, cudaStream_t s,
                                   bool pdl_first) {
     if (n <= 0) {
-        if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(unsigned long long), s);
+        if (total_dev) return fill_words(total_dev, 0u, sizeof(unsigned long long), s);
         return cudaSuccess;
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
@@ -641,7 +641,7 @@ cudaError_t launch_emit_pairs(const ViewDesc *views_dev, int n_views, const uint
 
 cudaError_t launch_tile_ranges(const uint32_t *pair_keys, int64_t n_pairs, const ViewDesc *views_dev, int local_bits,
                                int mask_shift, uint2 *ranges, int64_t n_tiles, cudaStream_t s, int n_views) {
-    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+    cudaError_t e = fill_words(ranges, 0u, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess || n_pairs <= 0) return e;
     const uint32_t key_mask = mask_shift ? (1u << mask_shift) - 1u : 0xffffffffu;
     const int64_t threads = (n_pairs + RANGE_ITEMS - 1) / RANGE_ITEMS;

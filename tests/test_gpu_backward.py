@@ -317,11 +317,13 @@ def test_step_through_host_buffers_equals_device_calls(pinned, n_views):
 
 @pytest.mark.parametrize("pinned", [True, False])
 def test_pipelined_host_steps_equal_device_calls(pinned):
-    """cs_step_host_submit / cs_step_host_wait: three steps submitted back to back (each step's
-    inputs copied in and outputs copied out while the other slot's step computes) give, view by
-    view, the image of cs_forward bit for bit and the gradients of cs_backward up to the order of
-    the atomics, from pinned or pageable host memory; a ticket that was never submitted is
-    rejected."""
+    """cs_step_host_submit / cs_step_host_wait: seven steps submitted back to back over three
+    views (inputs copied in and outputs copied out while other steps compute, the three slots each
+    reused) give, step by step, the image of cs_forward bit for bit and the gradients of
+    cs_backward up to the order of the atomics, from pinned or pageable host memory; a ticket that
+    was never submitted is rejected; a step that fails in the worker thread (a backward with
+    alpha_max above 0.999) is reported, with its message, by the next wait, once, and the steps
+    after it still run."""
     import torch
     import paper_2411_14974_gb300 as cs
     from paper_2411_14974_gb300 import _binding as B
@@ -334,22 +336,36 @@ def test_pipelined_host_steps_equal_device_calls(pinned):
                      else torch.as_tensor(np.ascontiguousarray(a, np.float32)))
     scene_h = dict(points=pin(sc.points), delta=pin(sc.delta), sigma=pin(sc.sigma), opacity=pin(sc.opacity),
                    sh=pin(sc.sh))
-    imgs = [pin(np.full((1, 3, 64, 80), np.nan)) for _ in cams]
-    gs = [{f: pin(np.full(tuple(getattr(t, f).shape), np.nan)) for f in FIELDS} for _ in cams]
+    n_steps = 7
+    imgs = [pin(np.full((1, 3, 64, 80), np.nan)) for _ in range(n_steps)]
+    gs = [{f: pin(np.full(tuple(getattr(t, f).shape), np.nan)) for f in FIELDS} for _ in range(n_steps)]
     dls = [pin(G[v]) for v in range(3)]
-    tickets = [cs.step_host_submit(scene_h, sc.sh_degree, cam, cs.Settings(), dls[v], imgs[v], gs[v])
-               for v, cam in enumerate(cams)]
-    assert tickets == sorted(tickets) and len(set(tickets)) == 3
+    tickets = [cs.step_host_submit(scene_h, sc.sh_degree, cams[i % 3], cs.Settings(), dls[i % 3], imgs[i], gs[i])
+               for i in range(n_steps)]
+    assert tickets == sorted(tickets) and len(set(tickets)) == n_steps
     cs.step_host_wait(tickets[-1])
+    wants = []
     for v, cam in enumerate(cams):
         img, _, state = cs.forward(t, [cam], cs.Settings(), keep_state=True)
         want = cs.backward(state, torch.as_tensor(G[v], device=dev))
         torch.cuda.synchronize()
         state.release()
-        assert torch.equal(imgs[v], img.cpu()), v
+        wants.append((img.cpu(), {f: want[f].cpu().numpy() for f in FIELDS}))
+    for i in range(n_steps):
+        img, want = wants[i % 3]
+        assert torch.equal(imgs[i], img), i
         for f in FIELDS:
-            a, b = gs[v][f].numpy(), want[f].cpu().numpy()
-            assert np.isfinite(a).all(), (v, f)
-            assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-30), (v, f)
+            a, b = gs[i][f].numpy(), want[f]
+            assert np.isfinite(a).all(), (i, f)
+            assert np.abs(a - b).max() <= 1e-5 * (np.abs(b).max() + 1e-30), (i, f)
     with pytest.raises(B.CsError):
         cs.step_host_wait(tickets[-1] + 100)
+    # a queued step whose backward is refused: the wait reports it once, later steps still run
+    bad = cs.Settings(alpha_max=0.9999)
+    cs.step_host_submit(scene_h, sc.sh_degree, cams[0], bad, dls[0], imgs[0], gs[0])
+    imgs[1].fill_(float("nan"))
+    tk = cs.step_host_submit(scene_h, sc.sh_degree, cams[1], cs.Settings(), dls[1], imgs[1], gs[1])
+    with pytest.raises(B.CsError, match="alpha_max"):
+        cs.step_host_wait(tk)
+    cs.step_host_wait(tk)
+    assert torch.equal(imgs[1], wants[1][0])
