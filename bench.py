@@ -684,18 +684,23 @@ def run_ours(args):
         host_dL = dL.cpu().pin_memory()
         host_img = torch.empty((1, 3, H, W)).pin_memory()
         host_g = {k: torch.empty(tuple(v.shape)).pin_memory() for k, v in grads.items()}
-        ne = max(3, min(args.steps, 8))
+        ne = max(10, min(args.steps, 20))
         h2d = sum(v.numel() * 4 for v in host_scene.values()) + host_dL.numel() * 4
         d2h = host_img.numel() * 4 + sum(v.numel() * 4 for v in host_g.values())
         # one call at a time (cs_step_host: every step waits for the one before to end)
-        cs.step_host(host_scene, sc.sh_degree, [cams[0]], settings, host_dL, host_img, host_g, local)
+        for i in range(args.warmup):
+            cs.step_host(host_scene, sc.sh_degree, [cams[0]], settings, host_dL, host_img, host_g, local)
         t0 = time.perf_counter()
         for i in range(ne):
             cs.step_host(host_scene, sc.sh_degree, [cams[i % len(cams)]], settings, host_dL, host_img, host_g, local)
         sync_s = (time.perf_counter() - t0) / ne
-        # pipelined (cs_step_host_submit / wait): each step's scene upload overlaps the step before;
-        # every step still uploads its scene and cotangent and writes its image and gradients
-        tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[0], settings, host_dL, host_img, host_g, local)
+        # pipelined (cs_step_host_submit / wait): later steps' uploads and earlier steps' downloads
+        # overlap each step's compute; every step still uploads its scene and cotangent and writes
+        # its image and gradients.  Warm-up: the context's memory pool settles on the buffers three
+        # steps in flight need within about ten steps
+        for i in range(max(args.warmup, 10)):
+            tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[i % len(cams)], settings, host_dL, host_img,
+                                     host_g, local)
         cs.step_host_wait(tk, local)
         t0 = time.perf_counter()
         for i in range(ne):
