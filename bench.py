@@ -599,13 +599,22 @@ def run_ours(args):
             return t["lines_passed"] + 3 * t["passed"] + (2 * t["contributing"] if backward else 0)
 
         # FP32 pipe instructions: per visited pair 2 FMA + 1 max per line; per evaluated pair one
-        # subtract and one add per line plus about 12 for the sigmoid, clamp and compositing
-        def fp32_ops(t):
-            return 3 * t["lines_visited"] + 2 * t["lines_passed"] + 12 * t["passed"]
+        # subtract and one add per line plus about 12 for the sigmoid, clamp and compositing.  The
+        # backward repeats that and, per contributing pair, does the adjoint of Eq. 5 and of the
+        # indicator: T in front (1 subtract, 1 multiply), dL/dalpha (3 for dL/dC . c, 2 more),
+        # the colour gradient (4) and its accumulation (3), the colour behind (1), the opacity
+        # gradient and its sum (2), dI and d(sigma' phi) (5), the sigma' gradient and its sum (2),
+        # dphi (2): 26; per hull line the softmax weight times dphi (1) and the sums of g, g x and
+        # g y (3): 4 T, T taken as the mean hull size of the evaluated pairs
+        def fp32_ops(t, backward=False):
+            n = 3 * t["lines_visited"] + 2 * t["lines_passed"] + 12 * t["passed"]
+            if backward and t["passed"]:
+                n += 26 * t["contributing"] + 4 * t["contributing"] * t["lines_passed"] / t["passed"]
+            return n
 
         tot = tots[dom]
         mufu = mufu_ops(tot, dom != "blend")
-        fp32 = fp32_ops(tot)
+        fp32 = fp32_ops(tot, dom != "blend")
         # peaks: the per-SM rates of the transcendental unit and the FP32 pipe measured on this
         # GPU (clock64 microbenchmark), times the SM count, at the maximum SM clock sampled
         rates = cs.alu_rates(local)
@@ -670,7 +679,7 @@ def run_ours(args):
         for st_name in ("blend", "blend_backward"):
             tb = breakdown[st_name] / 1e3
             mf = mufu_ops(tots[st_name], st_name != "blend") / tb / 1e9 / mufu_peak
-            ff = fp32_ops(tots[st_name]) / tb / 1e9 / fp32_peak
+            ff = fp32_ops(tots[st_name], st_name != "blend") / tb / 1e9 / fp32_peak
             stages[st_name] = dict(bound="alu", mufu_frac=mf, fp32_frac=ff, frac=max(mf, ff))
         # end to end: each stage's time at its own bound, summed, over the measured step
         at_peak_s = sum(stages[k]["frac"] * breakdown[k] / 1e3 for k in stages)
@@ -696,9 +705,9 @@ def run_ours(args):
         sync_s = (time.perf_counter() - t0) / ne
         # pipelined (cs_step_host_submit / wait): later steps' uploads and earlier steps' downloads
         # overlap each step's compute; every step still uploads its scene and cotangent and writes
-        # its image and gradients.  Warm-up: the context's memory pool settles on the buffers three
-        # steps in flight need within about ten steps
-        for i in range(max(args.warmup, 10)):
+        # its image and gradients.  Warm-up: the context's memory pool settles on the buffers of
+        # three steps in flight within about ten steps
+        for i in range(max(args.warmup, 20)):
             tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[i % len(cams)], settings, host_dL, host_img,
                                      host_g, local)
         cs.step_host_wait(tk, local)

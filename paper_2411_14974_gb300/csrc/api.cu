@@ -205,10 +205,21 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
     delete ctx;
 }
 
+// Allocation sizes above 1 MiB are rounded up to one of eight sizes per power of two (at most
+// 12.5% more): buffers whose sizes change a little from call to call (the pair lists of different
+// views) then reuse the pool's blocks instead of making it map more memory, which takes the host
+// about a millisecond per call.
+static size_t size_class(size_t bytes) {
+    if (bytes <= ((size_t)1 << 20)) return (bytes + 255) & ~(size_t)255;
+    const int lg = 63 - __builtin_clzll((unsigned long long)bytes);
+    const size_t q = (size_t)1 << (lg - 3);
+    return (bytes + q - 1) & ~(q - 1);
+}
+
 cudaError_t cs::pool_alloc(cs_context *ctx, void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
-    bytes = (bytes + 255) & ~(size_t)255;
+    bytes = size_class(bytes);
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
 #if CS_CHECKED
     // checked builds hand out every buffer filled with 0xff bytes (NaN as float): a read of a
