@@ -22,7 +22,10 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
                                                                      PreprocessGrads out) {
     constexpr int NB = (DEG + 1) * (DEG + 1);
     constexpr int PW = K * 3, SW = NB * 3;           // words per convex
-    constexpr int PS = PW | 1, SS = SW | 1;          // odd strides: no bank conflicts
+    // the block's point gradients are staged contiguously (as in the output, so that they leave
+    // with 16-byte stores); the separate 16-bit-storage SH gradients at an odd stride (no bank
+    // conflicts)
+    constexpr int PS = PW, SS = SW | 1;
     constexpr int esz = STG == CS_STORE_F32 ? 4 : 2;
     constexpr bool CHUNKED = (SW * esz) % 16 == 0;   // degrees 1 and 3: 16-byte chunk layout possible
     constexpr bool IN_PLACE = !ATOMIC && STG == CS_STORE_F32;  // SH gradients overwrite the staged SH
@@ -38,8 +41,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
     const int sh_stride = stage_sh<STG>(ssh, vd.sh, i0, cnt, SW);
     if (!ATOMIC) {  // the gradients to add to: the buffers' contents, or zero when they are written
         if (out.dpoints)
-            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS)
-                s_dp[(q / PW) * PS + q % PW] = out.write ? 0.f : out.dpoints[i0 * PW + q];
+            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) s_dp[q] = out.write ? 0.f : out.dpoints[i0 * PW + q];
         if (SEP_DSH && out.dsh)
             for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS)
                 s_dsh[(q / SW) * SS + q % SW] = out.write ? 0.f : out.dsh[i0 * SW + q];
@@ -121,22 +123,22 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
         const float kappa = g * delta * LOG2E;
 
         // lines -> hull vertices -> projected points
-        float hu[KMAX], hv[KMAX];
+        float hu[K], hv[K];
 #pragma unroll
-        for (int t = 0; t < KMAX; ++t)
+        for (int t = 0; t < K; ++t)
             if (t < T) select_point<K>(u, v, hull_pack_index(hull, t), hu[t], hv[t]);
         const float ax = hu[0], ay = hv[0];
         float dkappa = 0.f;
-        float dhu[KMAX], dhv[KMAX];
+        float dhu[K], dhv[K];
 #pragma unroll
-        for (int t = 0; t < KMAX; ++t) dhu[t] = dhv[t] = 0.f;
+        for (int t = 0; t < K; ++t) dhu[t] = dhv[t] = 0.f;
 #pragma unroll
-        for (int t = 0; t < KMAX; ++t) {
+        for (int t = 0; t < K; ++t) {
             if (t >= T) break;
             const int t1 = (t + 1 == T) ? 0 : t + 1;
             float wx = hu[0], wy = hv[0];
 #pragma unroll
-            for (int q = 1; q < KMAX; ++q)
+            for (int q = 1; q < K; ++q)
                 if (q == t1) { wx = hu[q]; wy = hv[q]; }
             const float ex = wx - hu[t], ey = wy - hv[t];
             const float len = sqrtf(ex * ex + ey * ey);
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
             const float dux = (dnx - nx * nd) * il, duy = (dny - ny * nd) * il;
             const float dex = -duy, dey = dux;  // n = (ey, -ex)/|e|
 #pragma unroll
-            for (int q = 0; q < KMAX; ++q)
+            for (int q = 0; q < K; ++q)
                 if (q == t1) { dhu[q] += dex; dhv[q] += dey; }
             dhu[t] -= dex;
             dhv[t] -= dey;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
 #pragma unroll
         for (int k = 0; k < K; ++k) du[k] = dv[k] = 0.f;
 #pragma unroll
-        for (int t = 0; t < KMAX; ++t) {
+        for (int t = 0; t < K; ++t) {
             if (t >= T) break;
             const int k = hull_pack_index(hull, t);
 #pragma unroll
@@ -298,10 +300,38 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess_backward(const Vi
     }
     if (!ATOMIC) {
         __syncthreads();
-        if (out.dpoints)
-            for (int q = threadIdx.x; q < cnt * PW; q += PRE_THREADS) out.dpoints[i0 * PW + q] = s_dp[(q / PW) * PS + q % PW];
+        if (out.dpoints) {
+            // 16-byte stores from where the block's range starts on a 16-byte boundary
+            float *dst = out.dpoints + i0 * PW;
+            const int n = cnt * PW;
+            const int head = min(n, (int)(((16u - ((uintptr_t)dst & 15u)) & 15u) / 4u));
+            const int n4 = (n - head) / 4;
+            for (int q = threadIdx.x; q < head; q += PRE_THREADS) dst[q] = s_dp[q];
+            float4 *d4 = reinterpret_cast<float4 *>(dst + head);
+            for (int q = threadIdx.x; q < n4; q += PRE_THREADS)
+                d4[q] = make_float4(s_dp[head + 4 * q], s_dp[head + 4 * q + 1], s_dp[head + 4 * q + 2],
+                                    s_dp[head + 4 * q + 3]);
+            for (int q = head + 4 * n4 + threadIdx.x; q < n; q += PRE_THREADS) dst[q] = s_dp[q];
+        }
         if (out.dsh) {
-            if (IN_PLACE) {
+            float *dst = out.dsh + i0 * SW;
+            if (IN_PLACE && sh_stride && ((uintptr_t)dst & 15u) == 0) {
+                // the staged chunks (sh_stride 16-byte chunks per convex) leave with 16-byte stores
+                constexpr int C = SW / 4;
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(ssh);
+                float4 *d4 = reinterpret_cast<float4 *>(dst);
+                for (int f = threadIdx.x; f < cnt * C; f += PRE_THREADS) {
+                    const int t = f / C;
+                    const uint4 v = s4[t * sh_stride + (f - t * C)];
+                    float4 d = make_float4(__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z),
+                                           __uint_as_float(v.w));
+                    if (!out.write) {
+                        const float4 o = d4[f];
+                        d.x += o.x; d.y += o.y; d.z += o.z; d.w += o.w;
+                    }
+                    d4[f] = d;
+                }
+            } else if (IN_PLACE) {
                 for (int q = threadIdx.x; q < cnt * SW; q += PRE_THREADS) {
                     const int t = q / SW;
                     const float d = sh_stride ? ssh[t * sh_stride * 4 + (q - t * SW)] : ssh[q];
