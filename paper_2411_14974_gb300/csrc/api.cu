@@ -402,6 +402,9 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
     uint64_t P = 0;
     int depth_bits = 0;
     bool in_b = false;
+    // one persistent blend launch over all views, with a completion flag per view (serving loop)
+    const bool persist = s->view_flags && s->st.tile_split == 0 && V <= MAX_ORDER_VIEWS &&
+                         s->view_done.size() == (size_t)V;
     uint32_t max_view_tiles = 1;
     for (int v = 0; v < V; ++v) {
         const uint32_t t = (uint32_t)(s->views[v].tiles_x * s->views[v].tiles_y);
@@ -551,11 +554,16 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
                                   stream, V),
                "tile ranges");
     }
-    if (s->st.tile_split == 0 && s->view_done.empty() && tiles > 0) {
-        // the blends launch the tiles longest pair list first (both passes use the order)
+    if (s->st.tile_split == 0 && (s->view_done.empty() || persist) && tiles > 0) {
+        // the blends launch the tiles longest pair list first (both passes use the order); the
+        // persistent launch of several views takes them view by view, and its counters (tile
+        // queue, tiles done per view) follow the order, zeroed by the same kernel
         StageTimer tm(ctx, CS_STAGE_TILE_SORT, stream);
-        CS_TRY(pool_alloc(ctx, (void **)&s->tile_order, (size_t)tiles * 4, stream), "alloc");
-        CS_TRY(launch_tile_order(s->ranges, tiles, s->tile_order, stream), "tile order");
+        const int n_zero = persist ? 1 + V : 0;
+        CS_TRY(pool_alloc(ctx, (void **)&s->tile_order, ((size_t)tiles + n_zero) * 4, stream), "alloc");
+        CS_TRY(launch_tile_order(s->ranges, tiles, s->tile_order, s->views_dev, V, persist, s->tile_order + tiles,
+                                 n_zero, stream),
+               "tile order");
     }
     if (s->st.tile_split > 0 && P > 0) {
         // tile split: which tiles are heavy, their chunk slots, the work items; the totals size the
@@ -614,7 +622,16 @@ cs_status cs::run_forward(cs_context *ctx, cs_fwd_state *s, cudaStream_t stream)
         a.n_pairs = (uint32_t)P;
         a.n_records = (uint32_t)R;
         set_split_args(a, s);
-        if (s->view_done.size() == (size_t)V && !a.split) {
+        if (persist && s->tile_order) {
+            // one persistent launch over all views; each view's flag is raised when its last tile
+            // is written (the events, recorded after the launch, mark the whole batch)
+            a.queue = s->tile_order + tiles;
+            a.view_tiles_done = s->tile_order + tiles + 1;
+            a.view_flags = s->view_flags;
+            a.flag_value = s->flag_value;
+            CS_TRY(launch_blend_forward(a, stream), "blend");
+            for (int v = 0; v < V; ++v) CS_TRY(cudaEventRecord(s->view_done[v], stream), "record view");
+        } else if (s->view_done.size() == (size_t)V && !a.split) {
             for (int v = 0; v < V; ++v) {  // one launch per view, each view's completion recorded
                 const ViewDesc &vd = s->views[v];
                 BlendArgs av = a;

@@ -28,6 +28,8 @@
 // the convex's gradient record by one coalesced atomic instruction per (warp, record).
 #include "cs_common.cuh"
 
+#include <atomic>
+
 namespace cs {
 namespace {
 
@@ -497,6 +499,11 @@ __device__ __forceinline__ void walk_forward(const BlendArgs &a, uint32_t lo, ui
 // Chunk state: [slot][5][256] floats, word 0-2 colour, 3 transmittance, 4 last pair + 1, for the
 // tile pixel with index split_pixel(x, y) (x, y within the tile).
 constexpr int MODE_PLAIN = 0, MODE_CHUNK = 1, MODE_MERGE = 2;
+// MODE_PERSIST: one persistent launch over the tiles of several views (the batches of the serving
+// loop): a grid of the CTAs resident at once, each taking the next tile of the order from a
+// counter in device memory; the CTA that finishes a view's last tile raises the view's flag in
+// mapped host memory, so that each view is known complete as soon as its image is written.
+constexpr int MODE_PERSIST = 3;
 constexpr int STATE_WORDS = 5;
 constexpr uint32_t NO_SLOT = 0xffffffffu;
 
@@ -507,10 +514,66 @@ __device__ __forceinline__ float *state_word(const BlendArgs &a, uint32_t slot, 
     return a.chunk_state + ((size_t)slot * STATE_WORDS + word) * (TILE * TILE) + pix;
 }
 
+// the forward's outputs of pixel (px, py): colour over the background, final transmittance, last
+// contributor
+__device__ __forceinline__ void write_pixel(const ViewDesc &vd, const Settings &st, int px, int py, const FwdPixel &q) {
+    const size_t hw = (size_t)vd.width * vd.height, pix = (size_t)py * vd.width + px;
+    vd.image[pix] = fmaf(q.T, st.bg[0], q.C0);
+    vd.image[hw + pix] = fmaf(q.T, st.bg[1], q.C1);
+    vd.image[2 * hw + pix] = fmaf(q.T, st.bg[2], q.C2);
+    if (vd.t_final) vd.t_final[pix] = q.T;
+    vd.n_last[pix] = q.last;
+}
+
+// The whole forward of one 8x4 pixel block (column w & 1, row w >> 1 of tile g) by one warp: the
+// walk over the tile's pairs and the outputs of the lane's pixel.
+template <bool COUNT, int K>
+__device__ __forceinline__ void forward_block(const BlendArgs &a, uint32_t g, int w, int lane, float4 *wrec,
+                                              uint32_t *sidx, unsigned long long (&cnt)[NCOUNT]) {
+    const ViewDesc &vd = a.views[find_view(a.views, a.n_views, g)];
+    int tx, ty;
+    tile_of(vd, g, tx, ty);
+    const int bx = tx * TILE + (w & 1) * 8, by = ty * TILE + (w >> 1) * 4;
+    const int px = bx + (lane & 7), py = by + (lane >> 3);
+    const bool inside = px < vd.width && py < vd.height;
+    const float lx = (float)(lane & 7) + 0.5f, ly = (float)(lane >> 3) + 0.5f;
+    uint2 range = a.ranges[g];
+    if (!checked(range.x <= range.y && range.y <= a.n_pairs, CS_BAD_RANGE)) range = make_uint2(0, 0);
+    FwdPixel q{1.0f, 0.f, 0.f, 0.f, 0u, !inside};
+    if (COUNT && inside) cnt[5]++;
+    walk_forward<COUNT, K>(a, range.x, range.y, w, lane, (float)bx, (float)by, lx, ly, wrec, sidx, q, cnt);
+    if (inside) write_pixel(vd, a.st, px, py, q);
+}
+
 template <bool COUNT, int K, int MODE>
 __global__ void __launch_bounds__(FWD_THREADS, 4) k_blend_forward(BlendArgs a, unsigned long long *counts) {
     __shared__ float4 srec[FWD_THREADS / 32][STAGE_F4<K>];
     __shared__ uint32_t sidx_all[FWD_THREADS / 32][32];
+    if (MODE == MODE_PERSIST) {
+        __shared__ uint32_t s_item;
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        unsigned long long cnt[NCOUNT] = {0, 0, 0, 0, 0, 0};
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1u);
+            __syncthreads();
+            const uint32_t item = s_item;
+            __syncthreads();  // every thread has the item before the next one is taken
+            if (item >= a.n_tiles) break;
+            const uint32_t g = a.tile_order[item];
+            forward_block<false, K>(a, g, w, lane, srec[w], sidx_all[w], cnt);
+            __threadfence();  // this thread's pixels, visible on the device before the count below
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int v = find_view(a.views, a.n_views, g);
+                const uint32_t tiles = (uint32_t)(a.views[v].tiles_x * a.views[v].tiles_y);
+                if (atomicAdd(a.view_tiles_done + v, 1u) + 1u == tiles) {  // the view's last tile
+                    __threadfence_system();
+                    *reinterpret_cast<volatile uint32_t *>(a.view_flags + v) = a.flag_value;
+                }
+            }
+        }
+        return;
+    }
     uint32_t g, chunk = 0, slot = NO_SLOT;
     if (MODE == MODE_PLAIN) {
         g = a.tile_order ? a.tile_order[blockIdx.x] : a.tile_offset + blockIdx.x;
@@ -901,6 +964,12 @@ __device__ __forceinline__ uint32_t order_class(const uint2 &r) {
     const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
     return (uint32_t)__clz(len + 1u);  // 31 for an empty tile, smaller for longer lists
 }
+// the class of tile g in the view-by-view order: its view's classes come after those of the views
+// before it
+__device__ __forceinline__ uint32_t order_class_by_view(const uint2 *ranges, const ViewDesc *views, int n_views,
+                                                        uint32_t g) {
+    return (uint32_t)find_view(views, n_views, g) * TILE_ORDER_CLASSES + order_class(ranges[g]);
+}
 
 // One CTA: a histogram of the classes, their exclusive scan, then each tile placed at the next free
 // slot of its class.  Lanes of a warp that share a class take their slots with one shared atomic.
@@ -918,10 +987,17 @@ __device__ __forceinline__ uint32_t order_slot(uint32_t *counter, uint32_t c, bo
     return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
+constexpr int ORDER_CLASSES_MAX = TILE_ORDER_CLASSES * MAX_ORDER_VIEWS;
+static_assert(ORDER_CLASSES_MAX == ORDER_THREADS, "one class per thread in the scan");
+
 __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(const uint2 *__restrict__ ranges, uint32_t n_tiles,
-                                                            uint32_t *__restrict__ order) {
-    __shared__ uint32_t count[TILE_ORDER_CLASSES], next[TILE_ORDER_CLASSES];
-    if (threadIdx.x < TILE_ORDER_CLASSES) count[threadIdx.x] = 0;
+                                                            uint32_t *__restrict__ order,
+                                                            const ViewDesc *__restrict__ views, int n_views,
+                                                            bool by_view, uint32_t *zero_words, int n_zero) {
+    __shared__ uint32_t count[ORDER_CLASSES_MAX], next[ORDER_CLASSES_MAX], wsum[ORDER_THREADS / 32];
+    const int n_classes = by_view ? TILE_ORDER_CLASSES * n_views : TILE_ORDER_CLASSES;
+    count[threadIdx.x] = 0;
+    for (int q = threadIdx.x; q < n_zero; q += ORDER_THREADS) zero_words[q] = 0u;
     __syncthreads();
     // ORDER_PER tiles per thread per round, their ranges loaded together (one load latency a round);
     // the bounds are the same for every lane of a warp, so the warp-wide votes see all 32 lanes
@@ -931,7 +1007,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(const uint2 *__res
 #pragma unroll
         for (int j = 0; j < ORDER_PER; ++j) {
             const uint32_t g = base + j * ORDER_THREADS + threadIdx.x;
-            c[j] = g < n_tiles ? order_class(ranges[g]) : 0u;
+            c[j] = g < n_tiles ? (by_view ? order_class_by_view(ranges, views, n_views, g) : order_class(ranges[g])) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < ORDER_PER; ++j) {
@@ -940,14 +1016,27 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(const uint2 *__res
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 32 class sizes
-        const uint32_t v = count[threadIdx.x];
+    {  // exclusive scan of the class sizes, one class per thread: within warps, then over them
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const uint32_t v = threadIdx.x < (unsigned)n_classes ? count[threadIdx.x] : 0u;
         uint32_t x = v;
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if ((int)threadIdx.x >= d) x += y;
+            if (lane >= d) x += y;
         }
-        next[threadIdx.x] = x - v;
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t t = wsum[lane];
+            uint32_t z = t;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, d);
+                if (lane >= d) z += y;
+            }
+            wsum[lane] = z - t;
+        }
+        __syncthreads();
+        next[threadIdx.x] = wsum[wid] + x - v;
     }
     __syncthreads();
     for (uint32_t base = 0; base < n_tiles; base += stride) {
@@ -955,7 +1044,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_tile_order(const uint2 *__res
 #pragma unroll
         for (int j = 0; j < ORDER_PER; ++j) {
             const uint32_t g = base + j * ORDER_THREADS + threadIdx.x;
-            c[j] = g < n_tiles ? order_class(ranges[g]) : 0u;
+            c[j] = g < n_tiles ? (by_view ? order_class_by_view(ranges, views, n_views, g) : order_class(ranges[g])) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < ORDER_PER; ++j) {
@@ -1006,8 +1095,33 @@ __global__ void k_split_items(const uint2 *__restrict__ ranges, uint32_t n_tiles
 
 }  // namespace
 
+// CTAs of a persistent launch: as many as are resident on the device at once (SMs x CTAs per SM
+// at the kernel's occupancy), taken once per device; 0 when the query fails
+template <typename F>
+static uint32_t resident_ctas(F kernel, int threads, std::atomic<uint32_t> (&cache)[64]) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    uint32_t n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
+            return 0;
+        n = (uint32_t)(sms * per_sm);
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 template <int K>
-static void blend_forward_k(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
+static cudaError_t blend_forward_k(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
+    if (a.view_flags && !counts && !a.split) {
+        static std::atomic<uint32_t> grid[64];
+        const uint32_t n = min(a.n_tiles, resident_ctas(k_blend_forward<false, K, MODE_PERSIST>, FWD_THREADS, grid));
+        if (n == 0) return cudaErrorInvalidConfiguration;
+        k_blend_forward<false, K, MODE_PERSIST><<<n, FWD_THREADS, 0, s>>>(a, nullptr);
+        return cudaSuccess;
+    }
     if (counts) {
         k_blend_forward<true, K, MODE_PLAIN><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, counts);
     } else if (a.split) {
@@ -1016,19 +1130,22 @@ static void blend_forward_k(const BlendArgs &a, cudaStream_t s, unsigned long lo
     } else {
         k_blend_forward<false, K, MODE_PLAIN><<<a.n_tiles, FWD_THREADS, 0, s>>>(a, nullptr);
     }
+    return cudaSuccess;
 }
 
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts) {
     if (a.n_tiles == 0) return cudaSuccess;
+    cudaError_t e;
     switch (a.k) {
-        case 3: blend_forward_k<3>(a, s, counts); break;
-        case 4: blend_forward_k<4>(a, s, counts); break;
-        case 5: blend_forward_k<5>(a, s, counts); break;
-        case 6: blend_forward_k<6>(a, s, counts); break;
-        case 7: blend_forward_k<7>(a, s, counts); break;
-        case 8: blend_forward_k<8>(a, s, counts); break;
+        case 3: e = blend_forward_k<3>(a, s, counts); break;
+        case 4: e = blend_forward_k<4>(a, s, counts); break;
+        case 5: e = blend_forward_k<5>(a, s, counts); break;
+        case 6: e = blend_forward_k<6>(a, s, counts); break;
+        case 7: e = blend_forward_k<7>(a, s, counts); break;
+        case 8: e = blend_forward_k<8>(a, s, counts); break;
         default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     count_launches(a.split && !counts ? (a.n_heavy ? 2 : 1) : 1);
     return cudaGetLastError();
 }
@@ -1063,9 +1180,11 @@ cudaError_t take_status_blend(unsigned *bits, cudaStream_t s) {
 #endif
 }
 
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, cudaStream_t s) {
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, const ViewDesc *views,
+                              int n_views, bool by_view, uint32_t *zero_words, int n_zero, cudaStream_t s) {
     if (n_tiles == 0) return cudaSuccess;
-    k_tile_order<<<1, ORDER_THREADS, 0, s>>>(ranges, n_tiles, order);
+    if (by_view && (n_views < 1 || n_views > MAX_ORDER_VIEWS)) return cudaErrorInvalidValue;
+    k_tile_order<<<1, ORDER_THREADS, 0, s>>>(ranges, n_tiles, order, views, n_views, by_view, zero_words, n_zero);
     count_launches(1);
     return cudaGetLastError();
 }

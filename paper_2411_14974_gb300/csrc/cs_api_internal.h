@@ -94,6 +94,11 @@ struct cs_fwd_state {
     // when not empty (one event per view): the forward blends view by view, in view order, and
     // records view_done[v] on the stream once view v's image is written
     std::vector<cudaEvent_t> view_done;
+    // when not NULL (set by the serving loop, with view_done, at most 32 views, no tile split):
+    // the views are blended by one persistent launch, which stores flag_value into view_flags[v]
+    // (mapped host memory, device address) once view v's image is written
+    uint32_t *view_flags = nullptr;
+    uint32_t flag_value = 0;
     // tile split (settings.tile_split > 0): work items, heavy tiles, slots and chunk states, kept
     // for the backward
     uint32_t *tile_order = nullptr;  // blend launch order of the tiles (longest lists first)

@@ -177,6 +177,14 @@ struct BlendArgs {
     // heavy tiles (tile, first slot) of the merge, each tile's first slot, the chunk states
     // launch order of the tiles (PLAIN mode; NULL: tile index order): longest pair lists first
     const uint32_t *tile_order = nullptr;
+    // one persistent launch over the tiles of all views (view_flags != NULL; the tile order view by
+    // view): each CTA takes the next tile of tile_order from *queue, counts the tiles it finishes
+    // per view in view_tiles_done (both zero when the launch starts) and, on a view's last tile,
+    // stores flag_value into view_flags[view] (mapped host memory) once the view's image is written
+    uint32_t *queue = nullptr;
+    uint32_t *view_tiles_done = nullptr;
+    uint32_t *view_flags = nullptr;
+    uint32_t flag_value = 0;
     uint32_t split = 0;
     const uint2 *split_items = nullptr;
     uint32_t n_items = 0;
@@ -198,10 +206,14 @@ cudaError_t launch_split_items(const uint2 *ranges, uint32_t n_tiles, uint32_t s
                                unsigned int *heavy_fill, uint32_t *slot_of_tile, cudaStream_t s);
 constexpr int SPLIT_STATE_FLOATS = 5 * 256;  // per chunk slot: 5 words for each pixel of a 16x16 tile
 // Launch order of the blend CTAs: the tiles by decreasing floor(log2(pairs + 1)) (order within a
-// class free), so that the longest pair lists start first and do not trail the grid.  One launch
-// of one CTA; order: n_tiles words.  Each tile's outputs do not depend on when its CTA runs.
+// class free), so that the longest pair lists start first and do not trail the grid; by_view: view
+// by view in view order (at most MAX_ORDER_VIEWS views), longest lists first within each.  One
+// launch of one CTA; order: n_tiles words.  Each tile's outputs do not depend on when its CTA
+// runs.  The kernel also zeroes the n_zero words at zero_words (the persistent blend's counters).
 constexpr int TILE_ORDER_CLASSES = 32;
-cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, cudaStream_t s);
+constexpr int MAX_ORDER_VIEWS = 32;
+cudaError_t launch_tile_order(const uint2 *ranges, uint32_t n_tiles, uint32_t *order, const ViewDesc *views,
+                              int n_views, bool by_view, uint32_t *zero_words, int n_zero, cudaStream_t s);
 // counts: NULL for the production kernels, else 6 zeroed uint64 counters for the instrumented ones
 cudaError_t launch_blend_forward(const BlendArgs &a, cudaStream_t s, unsigned long long *counts = nullptr);
 cudaError_t launch_blend_backward(const BlendArgs &a, const float *dL_dimage, int64_t image_stride,

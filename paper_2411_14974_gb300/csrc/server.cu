@@ -13,6 +13,7 @@
 //   finisher         waits for the batches in order and, within a batch, for each view's event,
 //                    posting each request's completion as soon as its own image is written; then
 //                    frees the batch's buffers and returns its memory to the budget.
+#include <cstring>
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -55,6 +56,10 @@ struct Batch {
     size_t est = 0;
     cs_status status = CS_OK;
     double weighted_views = 0.0;  // sum of N * pixels / (1920 * 1080) over its views
+    // with one persistent blend launch: the batch's flag slots (its stream's) and the value its
+    // launch stores there per view; NULL: per-view launches, completions from view_done
+    volatile uint32_t *flags = nullptr;
+    uint32_t seq = 0;
 };
 
 double ms_between(Clock::time_point a, Clock::time_point b) {
@@ -72,6 +77,9 @@ struct cs_server {
     cs_context *ctx = nullptr;
     cudaStream_t streams[2] = {nullptr, nullptr};
     int next_stream = 0;
+    // per stream, MAX_ORDER_VIEWS completion flags of the batch in flight on it (mapped pinned
+    // memory: host and device addresses)
+    uint32_t *flags_host = nullptr, *flags_dev = nullptr;
 
     std::mutex mu;
     std::condition_variable cv_work, cv_done, cv_mem, cv_poll;
@@ -207,8 +215,17 @@ void cs_server::run_worker() {
         }
         lk.unlock();
 
-        cudaStream_t stream = streams[next_stream];
+        const int sidx = next_stream;
+        cudaStream_t stream = streams[sidx];
         next_stream ^= 1;
+        if (s && flags_dev && b->reqs.size() <= (size_t)MAX_ORDER_VIEWS) {
+            // one persistent blend launch for the batch; its flags carry the batch's number, so
+            // that values left by the stream's earlier batches never read as complete
+            b->seq = (uint32_t)(n_batches + 1);
+            b->flags = flags_host + sidx * MAX_ORDER_VIEWS;
+            s->view_flags = flags_dev + sidx * MAX_ORDER_VIEWS;
+            s->flag_value = b->seq;
+        }
         if (s) {
             b->view_done.assign(b->reqs.size(), nullptr);
             for (cudaEvent_t &e : b->view_done)
@@ -257,8 +274,12 @@ void cs_server::run_finisher() {
             cudaEvent_t ev = b->view_done[v];
             cudaError_t e = cudaSuccess;
             if (ev && per_view) {
-                while ((e = cudaEventQuery(ev)) == cudaErrorNotReady)
+                // complete once the view's flag carries this batch's number (persistent launch) or
+                // its event has passed (per-view launches; with the persistent launch, the end of
+                // the whole batch)
+                while (!(b->flags && b->flags[v] == b->seq) && (e = cudaEventQuery(ev)) == cudaErrorNotReady)
                     std::this_thread::sleep_for(std::chrono::microseconds(20));
+                if (b->flags && b->flags[v] == b->seq) e = cudaSuccess;
                 if (e == cudaSuccess) {
                     std::lock_guard<std::mutex> lk(mu);
                     complete_locked(b->reqs[v], CS_OK, (int)b->reqs.size(), Clock::now());
@@ -336,6 +357,19 @@ extern "C" cs_status cs_server_create(int32_t device, size_t budget, int32_t max
     }
     uint64_t zero = 0;  // the pool is the server's own: its high-water mark counts from here
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    // completion flags of the persistent blend launches (without them: one launch per view)
+    const size_t fbytes = 2 * MAX_ORDER_VIEWS * sizeof(uint32_t);
+    if (cudaHostAlloc((void **)&srv->flags_host, fbytes, cudaHostAllocMapped) == cudaSuccess) {
+        memset(srv->flags_host, 0, fbytes);
+        if (cudaHostGetDevicePointer((void **)&srv->flags_dev, srv->flags_host, 0) != cudaSuccess) {
+            cudaFreeHost(srv->flags_host);
+            srv->flags_host = nullptr;
+            srv->flags_dev = nullptr;
+        }
+    } else {
+        srv->flags_host = nullptr;
+    }
+    cudaGetLastError();  // a failed flag allocation is not an error of the server
     cudaSetDevice(prev);
     srv->worker = std::thread([srv] { srv->run_worker(); });
     srv->finisher = std::thread([srv] { srv->run_finisher(); });
@@ -366,6 +400,7 @@ extern "C" void cs_server_destroy(cs_server *srv) {
             cudaStreamSynchronize(s);
             cudaStreamDestroy(s);
         }
+    if (srv->flags_host) cudaFreeHost(srv->flags_host);
     cudaSetDevice(prev);
     cs_context_destroy(srv->ctx);
     delete srv;
