@@ -370,10 +370,13 @@ cs_status cs_refine(cs_context *ctx, int64_t n, int32_t k, int32_t sh_degree, co
    estimates, or the server's memory pool's real usage when that is more) fits the memory
    budget; requests that arrive while earlier batches are on the GPU join the next batch as soon
    as memory frees up.  A batch is preprocessed, binned and sorted as one (the view index lives in
-   the tile key), then blended view by view, cheapest view first; each request completes as soon
-   as its own view's blend has run.  Batches alternate between two streams, at most one in flight
-   on each, so the preprocess and sorts of one overlap the blends of the previous one.  Each view's image is identical to
-   rendering it alone with cs_forward.
+   the tile key), then blended by one persistent launch (batches of at most 32 views; larger ones
+   launch one blend per view) that takes the tiles view by view, cheapest view first; each
+   request completes as soon as its own view's image is written (the launch raises a flag per
+   view in mapped host memory, which the server's finisher thread polls).  Batches alternate
+   between two streams, at most one in flight on each, so the preprocess and sorts of one overlap
+   the blends of the previous one.  Each view's image is identical to rendering it alone with
+   cs_forward.
    Images are written to caller-owned device buffers [3][H][W] that must stay alive until the
    request's completion has been polled.  All calls are thread-safe. */
 typedef struct cs_server cs_server;

@@ -6,13 +6,16 @@
 //                    views, same K, estimated transient memory within the budget left by the
 //                    batches still on the GPU), orders the batch's views by estimated cost
 //                    (smallest first), runs the batched forward (one preprocess, binning and sort
-//                    for all views, then one blend launch per view, each followed by that view's
-//                    completion event) on one of two streams and goes back for the next batch --
-//                    so the preprocess and sorts of batch k+1 overlap the blends of batch k (at
-//                    most one batch in flight per stream);
-//   finisher         waits for the batches in order and, within a batch, for each view's event,
-//                    posting each request's completion as soon as its own image is written; then
-//                    frees the batch's buffers and returns its memory to the budget.
+//                    for all views, then one persistent blend launch over the views' tiles, view
+//                    by view, which raises each view's flag in mapped host memory once the view's
+//                    image is written; batches of more than 32 views: one blend launch per view,
+//                    each followed by that view's event) on one of two streams and goes back for
+//                    the next batch -- so the preprocess and sorts of batch k+1 overlap the blends
+//                    of batch k (at most one batch in flight per stream);
+//   finisher         waits for the batches in order and, within a batch, for each view's flag (or
+//                    event), posting each request's completion as soon as its own image is
+//                    written; then frees the batch's buffers and returns its memory to the
+//                    budget.
 #include <cstring>
 #include <algorithm>
 #include <chrono>
