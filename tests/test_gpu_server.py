@@ -42,13 +42,17 @@ def _alone(scene_t, cam):
     return img[0]
 
 
-def test_results_alone_equal_results_in_the_mix():
+@pytest.mark.parametrize("max_batch, n_req", [(8, 24), (40, 64)])
+def test_results_alone_equal_results_in_the_mix(max_batch, n_req):
+    """Batches of up to 32 views are blended by one persistent launch with a completion flag per
+    view; larger ones (max_batch 40) by one launch per view: either way each image equals the view
+    rendered alone."""
     import torch
     import paper_2411_14974_gb300 as cs
     dev = torch.device("cuda:0")
     _, scenes = _scenes(dev)
-    reqs = _requests(24, 1)
-    with cs.Server(0, budget_bytes=4 << 30, max_batch=8) as srv:
+    reqs = _requests(n_req, 1)
+    with cs.Server(0, budget_bytes=4 << 30, max_batch=max_batch) as srv:
         sids = [srv.add_scene(s) for s in scenes]
         outs = {}
         for si, cam in reqs:
