@@ -261,10 +261,13 @@ def test_autograd_render_matches_direct_backward_after_buffers_are_freed():
         assert np.abs(got - want[f]).max() <= 1e-5 * scale, f
 
 
-@pytest.mark.parametrize("n_views", [1, 2])
-def test_backward_write_equals_accumulate_into_zeros(n_views):
+@pytest.mark.parametrize("n_views, offset", [(1, 0), (2, 0), (1, 1), (2, 3)])
+def test_backward_write_equals_accumulate_into_zeros(n_views, offset):
     """cs_backward_write writes the gradients (buffers full of NaN beforehand) and equals
-    cs_backward accumulating into zeroed buffers, up to the order of the blend's atomics."""
+    cs_backward accumulating into zeroed buffers, up to the order of the blend's atomics; with the
+    buffers `offset` floats into larger ones (4-byte but not 16-byte aligned), the 16-byte
+    write-out and the clears of several views write exactly the buffers (the floats around them
+    stay NaN)."""
     import torch
     import paper_2411_14974_gb300 as cs
     sc = syn.surface_scene(61, n=8_000, sh_degree=3)
@@ -274,7 +277,8 @@ def test_backward_write_equals_accumulate_into_zeros(n_views):
     G = torch.as_tensor(np.random.default_rng(63).uniform(-1, 1, (n_views, 3, 72, 96)).astype(np.float32), device=dev)
     _, _, state = cs.forward(t, cams, cs.Settings(), keep_state=True)
     acc = cs.backward(state, G)
-    junk = {f: torch.full(tuple(getattr(t, f).shape), float("nan"), device=dev) for f in FIELDS}
+    bases = {f: torch.full((getattr(t, f).numel() + offset + 5,), float("nan"), device=dev) for f in FIELDS}
+    junk = {f: bases[f][offset:offset + getattr(t, f).numel()].view(tuple(getattr(t, f).shape)) for f in FIELDS}
     wrote = cs.backward(state, G, junk, accumulate=False)
     torch.cuda.synchronize()
     state.release()
@@ -282,6 +286,8 @@ def test_backward_write_equals_accumulate_into_zeros(n_views):
         a, w = acc[f].cpu().numpy(), wrote[f].cpu().numpy()
         assert np.isfinite(w).all(), f
         assert np.abs(a - w).max() <= 1e-5 * (np.abs(a).max() + 1e-30), f
+        around = torch.cat([bases[f][:offset], bases[f][offset + getattr(t, f).numel():]])
+        assert torch.isnan(around).all(), f
 
 
 @pytest.mark.parametrize("pinned,n_views", [(True, 1), (False, 1), (True, 2)])
