@@ -1029,16 +1029,20 @@ extern "C" cs_status cs_step_host_submit(cs_context *ctx, const cs_scene *sh, co
     std::lock_guard<std::mutex> lk(ctx->host_mu);
     const bool bwd = dL_host != nullptr;
     cudaError_t e = cudaSuccess;
-    if (!ctx->upload_stream) {
-        e = cudaStreamCreateWithFlags(&ctx->upload_stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->compute_stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->download_stream, cudaStreamNonBlocking);
+    if (!ctx->upload_stream) {  // streams and events, each created once (kept if a later one fails)
+        if (!ctx->compute_stream) e = cudaStreamCreateWithFlags(&ctx->compute_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !ctx->download_stream)
+            e = cudaStreamCreateWithFlags(&ctx->download_stream, cudaStreamNonBlocking);
         for (auto &sl : ctx->host_slots) {
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+            if (e == cudaSuccess && !sl.uploaded) e = cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming);
+            if (e == cudaSuccess && !sl.computed) e = cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming);
+            if (e == cudaSuccess && !sl.done) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         }
+        // the upload stream last: once it exists, everything else does
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->upload_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return fail_cuda(e, "cs_step_host_submit: streams and events");
+    }
+    if (!ctx->host_worker.joinable()) {  // started with the first step (again if that failed)
         try {
             ctx->host_worker = std::thread(host_worker_loop, ctx);
         } catch (...) {
