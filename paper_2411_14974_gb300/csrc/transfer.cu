@@ -28,6 +28,7 @@ constexpr int VIEWS_PER_LAUNCH = 16;  // 16 descriptors: well inside the 4 KB of
 struct ViewBatch {
     ViewDesc v[VIEWS_PER_LAUNCH];
 };
+static_assert(sizeof(ViewBatch) <= 4000, "the descriptors of one launch fit the 4 KB of kernel parameters");
 
 __global__ void k_put_views(ViewBatch b, int n, ViewDesc *__restrict__ dst) {
     constexpr int WORDS = sizeof(ViewDesc) / 4;
