@@ -707,19 +707,25 @@ def run_ours(args):
         # overlap each step's compute; every step still uploads its scene and cotangent and writes
         # its image and gradients.  Warm-up: the context's memory pool settles on the buffers of
         # three steps in flight within about ten steps
-        for i in range(max(args.warmup, 20)):
+        for i in range(max(args.warmup, 30)):
             tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[i % len(cams)], settings, host_dL, host_img,
                                      host_g, local)
         cs.step_host_wait(tk, local)
-        t0 = time.perf_counter()
-        for i in range(ne):
-            tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[i % len(cams)], settings, host_dL, host_img,
-                                     host_g, local)
-        cs.step_host_wait(tk, local)
-        e2e_s = (time.perf_counter() - t0) / ne
+        # three blocks of ne steps, each drained at its end; the value is the median block (the host
+        # link is shared with the machine's other GPUs and processes, and one block can catch a
+        # stall that is not the library's), every block reported
+        blocks = []
+        for b in range(3):
+            t0 = time.perf_counter()
+            for i in range(ne):
+                tk = cs.step_host_submit(host_scene, sc.sh_degree, cams[i % len(cams)], settings, host_dL, host_img,
+                                         host_g, local)
+            cs.step_host_wait(tk, local)
+            blocks.append((time.perf_counter() - t0) / ne)
+        e2e_s = sorted(blocks)[1]
         out["e2e"] = dict(value=pixels_per_step / e2e_s / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
                           d2h_bytes_per_step=int(d2h), ms_per_step=e2e_s * 1e3, api="cs_step_host_submit",
-                          steps=ne)
+                          steps=ne, blocks_ms_per_step=[x * 1e3 for x in blocks], estimator="median of 3 blocks")
         out["e2e_sync"] = dict(value=pixels_per_step / sync_s / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
                                d2h_bytes_per_step=int(d2h), ms_per_step=sync_s * 1e3, api="cs_step_host")
         # 16-bit parameter storage (the light model) on the same scene and views
