@@ -2,16 +2,15 @@
 //
 // Forward: each warp an 8x4 pixel block, each thread one pixel, 128 threads per half tile (16x8;
 // 256 per 16x16 tile in the tile-split, counting and persistent variants); backward: 128 threads
-// per tile, each warp an 8x8 block, each thread two pixels (rows r and r + 4).  The warps work independently (no CTA barrier).  A warp walks the tile's
-// depth-ordered pairs, keeping those whose record's pixel box reaches its block (the block-mask
-// bit carried in the pair key, or the box itself), 32 at a time, and stages their records in its
-// shared-memory slice (the forward copies the 32 records with coalesced cp.async, four whole
-// records per instruction, and each lane then rewrites its own in place; the backward's lanes
-// load theirs with vector loads): each record is re-expressed relative to the warp's block
-// origin so that every line is two FMAs per pixel, and tested for whether any pixel of the block
-// can pass the line pre-test; the warp then evaluates only the records of the resulting ballot.
-// Per pixel and
-// convex (Eq. S1, S2 and 5):
+// per tile, each warp an 8x8 block, each thread two pixels (rows r and r + 4).  The warps work
+// independently (no CTA barrier).  A warp walks the tile's depth-ordered pairs, keeping those
+// whose record's pixel box reaches its block (the block-mask bit carried in the pair key, or the
+// box itself), 32 at a time, and stages their records in its shared-memory slice (the forward
+// copies the 32 records with coalesced cp.async, four whole records per instruction, and each
+// lane then rewrites its own in place; the backward's lanes load theirs with vector loads): each
+// record is re-expressed relative to the warp's block origin so that every line is two FMAs per
+// pixel, and tested for whether any pixel of the block can pass the line pre-test; the warp then
+// evaluates only the records of the resulting ballot.  Per pixel and convex (Eq. S1, S2 and 5):
 //     s_t  = log2(e) d delta L_t(q)                     (T lines, 2 FMA each)
 //     phi2 = max_t s_t + log2 sum_t 2^(s_t - max)       (= log2(e) phi)
 //     I    = 1 / (1 + 2^(d sigma phi2))                 (= Sigmoid(-d sigma phi))
