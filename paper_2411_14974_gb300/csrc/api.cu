@@ -173,21 +173,22 @@ extern "C" void cs_context_destroy(cs_context *ctx) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);
-    cudaDeviceSynchronize();
-    for (auto &r : ctx->prof) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
-    for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
-    if (ctx->host_worker.joinable()) {  // the worker enqueues what is queued, then ends
+    // first the worker of the pipelined host-buffer steps: it enqueues what is queued (using the
+    // context's pool, events and profiling records), then ends
+    if (ctx->host_worker.joinable()) {
         {
             std::lock_guard<std::mutex> lk(ctx->job_mu);
             ctx->worker_stop = true;
         }
         ctx->job_cv.notify_all();
         ctx->host_worker.join();
-        cudaDeviceSynchronize();
     }
+    cudaDeviceSynchronize();
+    for (auto &r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->free_events) cudaEventDestroy(e);
     for (auto &sl : ctx->host_slots) {
         if (sl.buf) cudaFree(sl.buf);
         if (sl.uploaded) cudaEventDestroy(sl.uploaded);
