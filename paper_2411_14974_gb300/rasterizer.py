@@ -70,8 +70,10 @@ def cameras_array(cams: Sequence) -> ctypes.Array:
 class Context:
     """Library context on one device (owns the stream-ordered memory pool of transient buffers and
     the forward's readback slot).  Calls on one context must not overlap, and ctypes releases the
-    interpreter lock during a call, so `get` gives each host thread its own context."""
-    _by_device: dict = {}
+    interpreter lock during a call, so `get` gives each host thread its own context, kept in the
+    thread's local storage: it is released when the thread ends and nothing else (a forward
+    state) still refers to it."""
+    _local = threading.local()
 
     def __init__(self, device: int = 0):
         h = ctypes.c_void_p()
@@ -81,10 +83,12 @@ class Context:
 
     @classmethod
     def get(cls, device: int = 0) -> "Context":
-        key = (int(device), threading.get_ident())
-        if key not in cls._by_device:
-            cls._by_device[key] = Context(device)
-        return cls._by_device[key]
+        by_device = getattr(cls._local, "by_device", None)
+        if by_device is None:
+            by_device = cls._local.by_device = {}
+        if int(device) not in by_device:
+            by_device[int(device)] = Context(device)
+        return by_device[int(device)]
 
     def __del__(self):
         try:

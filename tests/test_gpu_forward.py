@@ -318,6 +318,41 @@ def test_light_16bit_storage(dtype_name):
         state.release()
 
 
+def test_each_thread_gets_its_own_context_released_when_the_thread_ends():
+    """The binding gives every host thread its own library context (calls on one context must not
+    overlap); a thread's context renders like the main thread's and is released when the thread
+    ends."""
+    import gc
+    import threading
+    import weakref
+    import torch
+    import paper_2411_14974_gb300 as cs
+    from paper_2411_14974_gb300.rasterizer import Context
+    sc, cams = syn.workload("blob1k_128", seed=0)
+    dev = torch.device("cuda:0")
+    t = cs.SceneTensors.from_numpy(sc, dev)
+    want, _, _ = cs.forward(t, cams)
+    torch.cuda.synchronize()
+    seen = {}
+
+    def work():
+        img, _, _ = cs.forward(t, cams)
+        torch.cuda.synchronize()
+        seen["img"] = img
+        ctx = Context.get(0)
+        seen["same"] = ctx is Context.get(0)
+        seen["ref"] = weakref.ref(ctx)
+
+    th = threading.Thread(target=work)
+    th.start()
+    th.join()
+    gc.collect()
+    assert seen["same"]
+    assert seen["ref"]() is None, "the thread's context outlived the thread"
+    assert Context.get(0) is not None
+    assert torch.equal(seen["img"], want)
+
+
 def test_multi_view_equals_single_views():
     """Views are binned and sorted together (view index in the tile key); each view's image is the
     same, bit for bit, as rendering it alone."""
